@@ -1,0 +1,291 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each ``pin_*`` function takes an oracle library handle and returns ``(ok, detail)``.  The
+ordinary tests assert every pin holds for the real oracle; the mutation test rebuilds the
+oracle with one planted mistake at a time and asserts that some pin fails.  Nothing here
+reuses the oracle's arithmetic: references are normal-mode closed forms, a library ODE
+integrator (scipy's DOP853) on the paper's equations written as whole-array numpy, an
+arbitrary-precision brute force, fixed points, and exact invariants.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.integrate import solve_ivp
+
+import chain_inputs as ci
+import oracle
+import closed_form as cf
+
+PER, FIX = oracle.PERIODIC, oracle.FIXED
+ROE, HAR = oracle.ROESSLER, oracle.HARMONIC
+
+
+# ---- harmonic chain: closed forms ------------------------------------------------------
+
+def pin_harmonic_modal(lib, n=64, bc=PER, nsteps=1000, dt=0.01, kappa=1.3, omega0=0.7, tol=1e-12):
+    """RK4 on the harmonic chain equals R^n applied per normal mode (exact up to rounding)."""
+    y0 = ci.uniform_state(n, 2, seed=1000 + n + 7 * bc)
+    prm = oracle.params(kappa=kappa, omega0=omega0)
+    got = oracle.rk4_integrate(y0, HAR, bc, dt, nsteps, prm, lib=lib)
+    ref = cf.rk4_modal(y0, bc, kappa, omega0, dt, nsteps)
+    err = cf.rel_inf(got, ref)
+    return err < tol, f"harmonic modal n={n} bc={bc}: rel err {err:.3e} (tol {tol:g})"
+
+
+def pin_harmonic_order4(lib, n=32, bc=PER, T=2.0, kappa=1.0, omega0=1.0):
+    """Error against the exact flow shrinks 16x per halving of dt (fourth order)."""
+    y0 = ci.uniform_state(n, 2, seed=2000 + n + bc)
+    prm = oracle.params(kappa=kappa, omega0=omega0)
+    exact = cf.exact_flow(y0, bc, kappa, omega0, T)
+    errs = []
+    for dt in (0.05, 0.025, 0.0125):
+        got = oracle.rk4_integrate(y0, HAR, bc, dt, int(round(T / dt)), prm, lib=lib)
+        errs.append(cf.rel_inf(got, exact))
+    orders = [float(np.log2(errs[i] / errs[i + 1])) for i in range(2)]
+    ok = all(3.85 < p < 4.2 for p in orders)
+    return ok, f"harmonic order bc={bc}: errors {errs}, observed orders {orders}"
+
+
+def pin_harmonic_energy(lib, n=48, bc=PER, nsteps=1000, dt=0.05, kappa=1.1, omega0=0.9, tol=1e-12):
+    """Energy of the initial state equals the modal sum, and after n steps equals
+    sum_m E_m(0) rho(h_m)^n (RK4's exact per-mode energy factor)."""
+    y0 = ci.uniform_state(n, 2, seed=3000 + n + bc)
+    prm = oracle.params(kappa=kappa, omega0=omega0)
+    e0 = oracle.energy_harmonic(y0, bc, prm, lib=lib)
+    e0_ref = float(np.sum(cf.modal_energy(y0, bc, kappa, omega0)))
+    y = oracle.rk4_integrate(y0, HAR, bc, dt, nsteps, prm, lib=lib)
+    e1 = oracle.energy_harmonic(y, bc, prm, lib=lib)
+    e1_ref = cf.rk4_energy(y0, bc, kappa, omega0, dt, nsteps)
+    r0 = abs(e0 - e0_ref) / e0_ref
+    r1 = abs(e1 - e1_ref) / e1_ref
+    drift = abs(e1_ref - e0_ref) / e0_ref
+    ok = r0 < tol and r1 < tol and drift > 100 * tol  # the drift itself must be resolved
+    return ok, f"energy bc={bc}: E0 rel {r0:.2e}, En rel {r1:.2e}, modal drift {drift:.2e}"
+
+
+# ---- Roessler chain: fixed points, library integrator, special cases ----------------
+
+def roessler_fixed_points(a=0.2, b=1.0, c=9.0):
+    """Equilibria of Eq. (6): y = -z, x = a z, a z^2 - c z + b = 0."""
+    disc = np.sqrt(c * c - 4 * a * b)
+    out = []
+    for z in ((c - disc) / (2 * a), (c + disc) / (2 * a)):
+        out.append(np.array([a * z, -z, z]))
+    return out
+
+
+def pin_roessler_fixed_point(lib, n=16, nsteps=1000, dt=0.01, tol=1e-12):
+    """A uniform periodic chain sitting at an equilibrium of Eq. (6) stays there."""
+    worst = 0.0
+    for fp in roessler_fixed_points():
+        y0 = np.tile(fp, (n, 1))
+        got = oracle.rk4_integrate(y0, ROE, PER, dt, nsteps, lib=lib)
+        worst = max(worst, cf.rel_inf(got, y0))
+    return worst < tol, f"Roessler equilibria drift {worst:.2e}"
+
+
+def roessler_chain_rhs(bc, kappa, a=0.2, b=1.0, c=9.0):
+    """Eq. (2) with f, g of Eqs. (6)-(7) as whole-array numpy (for scipy's integrator)."""
+    def F(_t, v):
+        r = v.reshape(-1, 3)
+        x, y, z = r[:, 0], r[:, 1], r[:, 2]
+        if bc == PER:
+            xl, xr = np.roll(x, 1), np.roll(x, -1)
+        else:
+            xl = np.concatenate(([0.0], x[:-1]))
+            xr = np.concatenate((x[1:], [0.0]))
+        out = np.empty_like(r)
+        out[:, 0] = -y - z + kappa * (xl - 2 * x + xr)
+        out[:, 1] = x + a * y
+        out[:, 2] = b + z * (x - c)
+        return out.reshape(-1)
+    return F
+
+
+def pin_roessler_vs_dop853(lib, n=6, bc=PER, kappa=1.0, T=0.5):
+    """RK4 converges at fourth order to scipy's DOP853 solution of the paper's equations."""
+    y0 = ci.uniform_state(n, 3, seed=4000 + n + bc)
+    sol = solve_ivp(roessler_chain_rhs(bc, kappa), (0.0, T), y0.reshape(-1), method="DOP853",
+                    rtol=1e-13, atol=1e-13)
+    ref = sol.y[:, -1].reshape(-1, 3)
+    prm = oracle.params(kappa=kappa)
+    errs = []
+    for dt in (0.025, 0.0125, 0.00625):
+        got = oracle.rk4_integrate(y0, ROE, bc, dt, int(round(T / dt)), prm, lib=lib)
+        errs.append(cf.rel_inf(got, ref))
+    orders = [float(np.log2(errs[i] / errs[i + 1])) for i in range(2)]
+    ok = all(3.85 < p < 4.25 for p in orders) and errs[-1] < 1e-7
+    return ok, f"Roessler vs DOP853 bc={bc}: errors {errs}, observed orders {orders}"
+
+
+def pin_roessler_uniform_single(lib, n=5, nsteps=300, dt=0.01):
+    """A uniform chain has zero coupling (Eq. (7) vanishes), so every site follows the
+    single-oscillator trajectory bit for bit; that trajectory converges to DOP853's."""
+    r0 = ci.uniform_state(1, 3, seed=5000)[0]
+    y0 = np.tile(r0, (n, 1))
+    got = oracle.rk4_integrate(y0, ROE, PER, dt, nsteps, lib=lib)
+    same = bool(np.all(got == got[0]))
+    T = nsteps * dt
+    sol = solve_ivp(roessler_chain_rhs(PER, 0.0), (0.0, T), r0, method="DOP853", rtol=1e-13, atol=1e-13)
+    err = cf.rel_inf(got[0], sol.y[:, -1])
+    return same and err < 1e-7, f"uniform chain: sites identical={same}, err vs DOP853 {err:.2e}"
+
+
+def pin_roessler_decoupled(lib, n=5, nsteps=200, dt=0.01):
+    """kappa = 0 decouples the sites: each equals a one-site periodic chain, bit for bit."""
+    y0 = ci.uniform_state(n, 3, seed=6000)
+    prm = oracle.params(kappa=0.0)
+    got = oracle.rk4_integrate(y0, ROE, PER, dt, nsteps, prm, lib=lib)
+    ok = True
+    for i in range(n):
+        one = oracle.rk4_integrate(y0[i:i + 1], ROE, PER, dt, nsteps, prm, lib=lib)
+        ok &= bool(np.array_equal(one[0], got[i]))
+    return ok, f"kappa=0 decoupling bitwise={ok}"
+
+
+# ---- brute force in arbitrary precision ------------------------------------------------
+
+def brute_force_rk4(y0, model, bc, prm, dt, nsteps, dps=40):
+    """Classical RK4 as a dense vector map in mpmath, neighbours from explicit lists."""
+    import mpmath as mp
+    mp.mp.dps = dps
+    a, b, c, kappa, omega0 = (mp.mpf(float(v)) for v in prm)
+    y = [[mp.mpf(float(v)) for v in row] for row in np.asarray(y0)]
+    n = len(y)
+    if bc == PER:
+        nb = [((i - 1) % n, (i + 1) % n) for i in range(n)]
+    else:
+        nb = [(i - 1 if i > 0 else None, i + 1 if i < n - 1 else None) for i in range(n)]
+    h = mp.mpf(float(dt))
+
+    def F(state):
+        out = []
+        for i, (l, r) in enumerate(nb):
+            xl = state[l][0] if l is not None else mp.mpf(0)
+            xr = state[r][0] if r is not None else mp.mpf(0)
+            s = state[i]
+            lap = xl + xr - 2 * s[0]
+            if model == ROE:
+                out.append([-s[1] - s[2] + kappa * lap, s[0] + a * s[1], b + s[2] * (s[0] - c)])
+            else:
+                out.append([s[1], -omega0 ** 2 * s[0] + kappa * lap])
+        return out
+
+    def axpy(u, alpha, v):
+        return [[ui + alpha * vi for ui, vi in zip(ur, vr)] for ur, vr in zip(u, v)]
+
+    for _ in range(nsteps):
+        k1 = F(y)
+        k2 = F(axpy(y, h / 2, k1))
+        k3 = F(axpy(y, h / 2, k2))
+        k4 = F(axpy(y, h, k3))
+        y = [[yi + h / 6 * (p + 2 * q + 2 * r + s) for yi, p, q, r, s in zip(*rows)]
+             for rows in zip(y, k1, k2, k3, k4)]
+    return np.array([[float(v) for v in row] for row in y])
+
+
+def pin_brute_force(lib, n=4, model=ROE, bc=PER, nsteps=100, dt=0.01, tol=1e-13):
+    D = oracle.dim(model)
+    y0 = ci.uniform_state(n, D, seed=7000 + n + 10 * model + bc)
+    prm = oracle.params(kappa=1.25, omega0=0.8)
+    got = oracle.rk4_integrate(y0, model, bc, dt, nsteps, prm, lib=lib)
+    ref = brute_force_rk4(y0, model, bc, prm, dt, nsteps)
+    err = cf.rel_inf(got, ref)
+    return err < tol, f"brute force n={n} model={model} bc={bc}: rel err {err:.2e}"
+
+
+# ---- exact invariants -------------------------------------------------------------------
+
+def pin_shift_invariance(lib, n=40, shift=7, nsteps=50):
+    """Periodic chain: integrating a cyclically shifted state gives the shifted result,
+    bit for bit (every site runs the same operations)."""
+    y0 = ci.uniform_state(n, 3, seed=8000)
+    a = oracle.rk4_integrate(np.roll(y0, shift, axis=0), ROE, PER, 0.01, nsteps, lib=lib)
+    b = np.roll(oracle.rk4_integrate(y0, ROE, PER, 0.01, nsteps, lib=lib), shift, axis=0)
+    ok = bool(np.array_equal(a, b))
+    return ok, f"shift invariance bitwise={ok}"
+
+
+def pin_reflection(lib, n=33, nsteps=100, tol=1e-12):
+    """Reflection i -> N+1-i maps solutions to solutions (to rounding: the oracle's
+    Laplacian adds its neighbours in a fixed left-right order)."""
+    worst = 0.0
+    for bc in (PER, FIX):
+        y0 = ci.uniform_state(n, 3, seed=8100 + bc)
+        a = oracle.rk4_integrate(y0[::-1], ROE, bc, 0.01, nsteps, lib=lib)[::-1]
+        b = oracle.rk4_integrate(y0, ROE, bc, 0.01, nsteps, lib=lib)
+        worst = max(worst, cf.rel_inf(a, b))
+    return worst < tol, f"reflection max rel err {worst:.2e}"
+
+
+def pin_dependency_cone(lib, n=64, site=24):
+    """Perturbing one site changes, after m steps, exactly the sites within 4m of it: each
+    of the four stages re-evaluates the coupling (the paper's halo of s sites per step,
+    Sec. 2.3).  A strong coupling and a large step keep the influence at distance 4m above
+    the rounding level, so the cone's edge is visible."""
+    y0 = ci.uniform_state(n, 3, seed=8200)
+    y1 = y0.copy()
+    y1[site, 0] += 0.5
+    prm = oracle.params(kappa=20.0)
+    ok = True
+    detail = []
+    for m in (1, 2, 3):
+        a = oracle.rk4_integrate(y0, ROE, FIX, 0.1, m, prm, lib=lib)
+        b = oracle.rk4_integrate(y1, ROE, FIX, 0.1, m, prm, lib=lib)
+        changed = np.nonzero(np.any(a != b, axis=1))[0]
+        lo, hi = int(changed.min()), int(changed.max())
+        detail.append((m, lo, hi))
+        ok &= (lo == site - 4 * m) and (hi == site + 4 * m)
+    return ok, f"dependency cone (m, lo, hi) = {detail}"
+
+
+# ---- general explicit tableaux (the technique applies to any explicit RK, Sec. 2) -----
+
+TABLEAUX = {
+    # name: (A, b, order)
+    "euler": (np.array([[0.0]]), np.array([1.0]), 1),
+    "heun2": (np.array([[0, 0], [1.0, 0]]), np.array([0.5, 0.5]), 2),
+    "kutta3": (np.array([[0, 0, 0], [0.5, 0, 0], [-1.0, 2.0, 0]]), np.array([1 / 6, 2 / 3, 1 / 6]), 3),
+    "rk4": (oracle.RK4_A, oracle.RK4_B, 4),
+    "rule38": (np.array([[0, 0, 0, 0], [1 / 3, 0, 0, 0], [-1 / 3, 1.0, 0, 0], [1.0, -1.0, 1.0, 0]]),
+               np.array([1 / 8, 3 / 8, 3 / 8, 1 / 8]), 4),
+}
+
+
+def pin_tableau_orders(lib, n=16, T=1.0):
+    """Each tableau's error against the exact harmonic flow falls as dt^order."""
+    y0 = ci.uniform_state(n, 2, seed=9000)
+    exact = cf.exact_flow(y0, PER, 1.0, 1.0, T)
+    detail = {}
+    ok = True
+    for name, (A, b, order) in TABLEAUX.items():
+        errs = []
+        for dt in (0.05, 0.025):
+            got = oracle.rk_integrate(y0, A, b, HAR, PER, dt, int(round(T / dt)), lib=lib)
+            errs.append(cf.rel_inf(got, exact))
+        p = np.log2(errs[0] / errs[1])
+        detail[name] = round(float(p), 3)
+        ok &= abs(p - order) < 0.2
+    return ok, f"observed orders {detail}"
+
+
+ALL_PINS = [
+    ("harmonic_modal_per", lambda lib: pin_harmonic_modal(lib, bc=PER)),
+    ("harmonic_modal_fix", lambda lib: pin_harmonic_modal(lib, bc=FIX)),
+    ("harmonic_order4_per", lambda lib: pin_harmonic_order4(lib, bc=PER)),
+    ("harmonic_order4_fix", lambda lib: pin_harmonic_order4(lib, bc=FIX)),
+    ("harmonic_energy_per", lambda lib: pin_harmonic_energy(lib, bc=PER)),
+    ("harmonic_energy_fix", lambda lib: pin_harmonic_energy(lib, bc=FIX)),
+    ("roessler_fixed_point", pin_roessler_fixed_point),
+    ("roessler_dop853_per", lambda lib: pin_roessler_vs_dop853(lib, bc=PER)),
+    ("roessler_dop853_fix", lambda lib: pin_roessler_vs_dop853(lib, bc=FIX, kappa=1.7)),
+    ("roessler_uniform", pin_roessler_uniform_single),
+    ("roessler_decoupled", pin_roessler_decoupled),
+    ("brute_roe_per", lambda lib: pin_brute_force(lib, model=ROE, bc=PER)),
+    ("brute_roe_fix", lambda lib: pin_brute_force(lib, model=ROE, bc=FIX)),
+    ("brute_har_fix", lambda lib: pin_brute_force(lib, model=HAR, bc=FIX)),
+    ("shift", pin_shift_invariance),
+    ("reflection", pin_reflection),
+    ("cone", pin_dependency_cone),
+    ("tableau_orders", pin_tableau_orders),
+]
