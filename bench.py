@@ -1,0 +1,347 @@
+"""Benchmark: site-steps/s of classical RK4 on the paper's coupled Roessler chain on GB300.
+
+Workload (one "step" of this benchmark = one pass of the whole hot path): a periodic Roessler
+chain (Eqs. (6)-(7), a = 0.2, b = 1, c = 9, kappa = 1) of N = 2^24 sites in FP64, i.i.d.
+uniform[-1, 1) initial state from the counter-based generator, advanced 1000 RK4 steps with
+dt = 0.01 by the temporally blocked kernel (tiling chosen by the autotuner), followed by one
+FP64 norm reduction with non-finite check.  The state (403 MB) and its ping-pong copy are
+larger than the 129 MB L2, so no flush is needed between steps.
+
+Printed: one JSON line (rank 0).  `value` = site-steps/s over all ranks; `roofline` refers to
+the blocked FP64 kernel, which is bound by the FP64 pipe (49 FP64 instructions per site-step
+against the measured FP64 FMA rate of this GPU); `e2e` measures the same through
+rk4_chain_integrate_host from pinned host memory; `cpu_baseline` is the serial C oracle on the
+host.  Extra keys report the FP32-Kahan path and a batch of uneven chains.
+
+`--impl reference` times the CPU oracle instead (the reference arm), on bounded samples.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_SITES = 1 << 24
+NSTEPS = 1000
+DT = 0.01
+SEED = 0x14120544
+D = 3
+HBM_GBS_FALLBACK = 6800.0
+# FP64 pipe rate measured on this GPU model with a dependent-free DFMA loop
+# (profiles/gb300_probe_pipes.md): 0.599e12 FP64 FMA instructions per second.
+FP64_INST_PEAK = 0.599e12
+FP32_INST_PEAK = 36.6e12
+FP64_INST_PER_SITE_STEP = 49     # 4 x 7 slope + 9 stage + 9 sum + 3 update
+FP32K_INST_PER_SITE_STEP = 61    # + 4 per component for the Kahan update
+# DRAM traffic per launch of the FP64 blocked kernel from an ncu capture, valid only for the
+# kernel sources whose hash is recorded next to it (else reported as null).
+TRAFFIC = {}
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("rk4_device.cuh", "rk4_tile.cuh", "k_blocked.cu"):
+        with open(os.path.join(ROOT, "paper_1412_0544_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                mhz.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def cpu_baseline(sample_sites: int = 1 << 22, sample_steps: int = 10) -> dict:
+    """The serial C oracle on the host (1 core) on a bounded sample of the workload."""
+    import chain_inputs as ci
+    import oracle
+    y0 = ci.uniform_state(sample_sites, D, seed=SEED)
+    oracle.load()
+    t0 = time.perf_counter()
+    oracle.rk4_integrate(y0, oracle.ROESSLER, oracle.PERIODIC, DT, sample_steps)
+    dt = time.perf_counter() - t0
+    return {"value": sample_sites * sample_steps / dt, "unit": "site-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"periodic Roessler chain N={sample_sites}, {sample_steps} RK4 steps, FP64, serial C oracle"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, timed on bounded samples of the same workload."""
+    from paper_1412_0544_gb300 import dist
+    rank, world, _ = dist.env_rank()
+    if rank != 0:
+        return 0
+    import chain_inputs as ci
+    import oracle
+    oracle.load()
+    sites, steps = 1 << 22, 2
+    y = ci.uniform_state(sites, D, seed=SEED)
+    for _ in range(args.warmup):
+        y = oracle.rk4_integrate(y, oracle.ROESSLER, oracle.PERIODIC, DT, steps)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        y = oracle.rk4_integrate(y, oracle.ROESSLER, oracle.PERIODIC, DT, steps)
+    el = time.perf_counter() - t0
+    value = sites * steps * args.steps / el
+    sample = f"periodic Roessler chain N={sites}, {steps} RK4 steps per step, FP64, serial C oracle"
+    line = {"impl": "reference", "metric": "site-steps/s", "value": value, "unit": "site-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "roessler_chain_fp64_N2^24_1000steps", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "site-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "site-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def time_integrate(rk, h, st, cp, ws, nsteps, reps, torch):
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        rk.rk4_chain_integrate(h, st, cp, ws, nsteps)
+    e1.record(s)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def fp32_kahan_extra(rk, torch, stream, n=N_SITES, nsteps=NSTEPS, reps=2):
+    """FP32 state + Kahan-compensated update, same chain (configs: FP32 at N=2^24)."""
+    h = rk.rk4_chain_create(rk.RK4_ROESSLER, rk.RK4_FP32_KAHAN, n, DT, rk.RK4_PERIODIC, None, stream)
+    try:
+        st = torch.empty((n, D), dtype=torch.float32, device="cuda")
+        rk.rk4_fill_uniform(st, n * D, SEED, 0, rk.RK4_FP32_KAHAN, stream)
+        cp = torch.zeros_like(st)
+        ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+        best = rk.rk4_chain_autotune(h, st.clone(), cp.clone(), ws, 32)
+        rk.rk4_chain_integrate(h, st, cp, ws, 2 * best["k"])
+        el = time_integrate(rk, h, st, cp, ws, nsteps, reps, torch)
+        sps = n * nsteps * reps / el
+        launches = -(-nsteps // best["k"])
+        return {"value": sps, "unit": "site-steps/s", "N": n, "steps": nsteps, "tiling": best,
+                "effective_state_GBs": sps * 2 * D * 4 / 1e9,
+                "hbm_traffic_GBs_est": sps * 4 * D * 4 * (1 + 8 * best["k"] / best["G"]) / best["k"] / 1e9,
+                "fp32_pipe_frac_of_measured": sps * FP32K_INST_PER_SITE_STEP / FP32_INST_PEAK,
+                "ms_per_launch": 1e3 * el / (reps * launches)}
+    finally:
+        rk.rk4_chain_destroy(h)
+
+
+def batch_extra(rk, torch, stream, precision, nsteps=NSTEPS):
+    """4096 chains, lengths log-uniform in [64, 65536], kappa ~ U[0.5, 2], mixed boundaries,
+    one persistent cooperative launch replayed from a CUDA graph."""
+    import chain_inputs as ci
+    lengths, kappa, bcs = ci.batch_spec(4096, seed=SEED)
+    total = int(lengths.sum())
+    h = rk.rk4_batch_create(rk.RK4_ROESSLER, precision, lengths, kappa, bcs, DT, None, stream)
+    try:
+        dt_ = torch.float32 if precision == rk.RK4_FP32_KAHAN else torch.float64
+        st = torch.empty((total, D), dtype=dt_, device="cuda")
+        rk.rk4_fill_uniform(st, total * D, SEED, 0, precision, stream)
+        cp = torch.zeros_like(st) if precision == rk.RK4_FP32_KAHAN else None
+        ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+        best = rk.rk4_chain_autotune(h, st.clone(), cp.clone() if cp is not None else None, ws, 32)
+        rk.rk4_chain_integrate(h, st, cp, ws, nsteps)  # capture + warm-up
+        el = time_integrate(rk, h, st, cp, ws, nsteps, 1, torch)
+        return {"value": total * nsteps / el, "unit": "site-steps/s", "chains": 4096, "sites": total,
+                "steps": nsteps, "tiling": best, "kernel": "persistent cooperative, CUDA graph"}
+    finally:
+        rk.rk4_chain_destroy(h)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP32 and batch side measurements")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tiling", default=None, help="block,v,k of the FP64 kernel instead of the autotuner's pick")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np  # noqa: F401
+    import torch
+
+    from paper_1412_0544_gb300 import dist
+    import paper_1412_0544_gb300 as rk
+
+    rank, world, local = dist.init("nccl")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    peaks = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", HBM_GBS_FALLBACK))
+
+    # --- the workload: one chain per rank (independent replicas, weak scaling) -------
+    n = N_SITES
+    h = rk.rk4_chain_create(rk.RK4_ROESSLER, rk.RK4_FP64, n, DT, rk.RK4_PERIODIC, None, stream)
+    st = torch.empty((n, D), dtype=torch.float64, device="cuda")
+    rk.rk4_fill_uniform(st, n * D, SEED, 0, rk.RK4_FP64, stream)
+    ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+    if args.tiling:
+        rk.rk4_chain_set_tiling(h, *[int(x) for x in args.tiling.split(",")])
+        tiling = rk.rk4_chain_get_tiling(h)
+    else:
+        tiling = rk.rk4_chain_autotune(h, st.clone(), None, ws, 16)
+    plan_launches = -(-NSTEPS // tiling["k"])
+    plan_launches += plan_launches % 2  # the plan keeps an even launch count when it can
+
+    def one_step():
+        rk.rk4_chain_integrate(h, st, None, ws, NSTEPS)
+        return rk.rk4_chain_energy(h, st, None, ws)[0]  # synchronises; checks for NaN/inf
+
+    for _ in range(args.warmup):
+        one_step()
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        e0.record(stream)
+        for _ in range(args.steps):
+            norm = one_step()
+        e1.record(stream)
+        e1.synchronize()
+    torch.cuda.synchronize()
+    dist.barrier()
+    el = dist.max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    site_steps = float(n) * NSTEPS * args.steps * world
+    value = site_steps / el
+
+    # kernel-only timing of the blocked kernel for the roofline (same stream, events)
+    reps = 2
+    el_k = time_integrate(rk, h, st, None, ws, NSTEPS, reps, torch)
+    launch_s = el_k / (reps * plan_launches)
+    sps_k = n * NSTEPS * reps / el_k
+    achieved_inst = sps_k * FP64_INST_PER_SITE_STEP / 1e9  # G FP64 instructions/s
+    khash = kernel_hash()
+    traffic = TRAFFIC.get(khash)
+    roofline = {"bound": "alu", "achieved": achieved_inst, "peak": FP64_INST_PEAK / 1e9,
+                "unit": "G FP64 inst/s", "frac": achieved_inst * 1e9 / FP64_INST_PEAK,
+                "traffic": traffic, "kernel": "k_blocked<double, Roessler>",
+                "per_unit": "49 FP64 instructions per interior site-step",
+                "launch_ms": launch_s * 1e3,
+                "peak_source": "measured FP64 FMA issue rate (probe), of measured",
+                "hbm_frac_effective_state": sps_k * 2 * D * 8 / 1e9 / hbm_peak}
+
+    # --- end to end through the C ABI with host buffers ------------------------------
+    host = torch.empty((n, D), dtype=torch.float64).pin_memory()
+    host.copy_(st.cpu())
+    dev2 = torch.empty_like(st)
+    rk.rk4_chain_integrate_host(h, host, None, dev2, None, ws, NSTEPS)  # warm
+    dist.barrier()
+    t0 = time.perf_counter()
+    e2e_steps = 2
+    for _ in range(e2e_steps):
+        rk.rk4_chain_integrate_host(h, host, None, dev2, None, ws, NSTEPS)
+    el_e2e = dist.max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": float(n) * NSTEPS * e2e_steps * world / el_e2e, "unit": "site-steps/s",
+           "h2d_bytes_per_step": n * D * 8, "d2h_bytes_per_step": n * D * 8,
+           "api": "rk4_chain_integrate_host (pinned host state in, result out)"}
+    del host, dev2
+
+    extras = {}
+    if not args.no_extras:
+        extras["fp32_kahan"] = fp32_kahan_extra(rk, torch, stream)
+        extras["batch_fp64"] = batch_extra(rk, torch, stream, rk.RK4_FP64, nsteps=200)
+        extras["batch_fp32_kahan"] = batch_extra(rk, torch, stream, rk.RK4_FP32_KAHAN, nsteps=200)
+    rk.rk4_chain_destroy(h)
+
+    out = None
+    if rank == 0:
+        out = {
+            "metric": "site-steps/s (RK4, fp64 & fp32-compensated) and % of GB300 HBM roofline",
+            "value": value, "unit": "site-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "roessler_chain_fp64_N2^24_1000steps", "sites": n, "rk4_steps_per_step": NSTEPS,
+                       "dt": DT, "boundary": "periodic", "tiling": tiling, "l2": "inputs larger than L2 (403 MB state)",
+                       "parallelism": f"replicas x{world}", "final_half_norm2": float(norm)},
+            "roofline": roofline,
+            "effective_state_GBs": value / world * 2 * D * 8 / 1e9,
+            "pct_hbm_roofline_effective": 100.0 * value / world * 2 * D * 8 / 1e9 / hbm_peak,
+            "clocks": clocks.summary(),
+            "e2e": e2e,
+            "gpu_launches": args.steps * (plan_launches + 2),
+            "kernel_hash": khash,
+        }
+        out.update(extras)
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out))
+    dist.barrier()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

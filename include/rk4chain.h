@@ -1,0 +1,200 @@
+/*
+ * rk4chain.h -- C ABI of librk4chain.so: classical fixed-step RK4 integration of long
+ * one-dimensional chains with nearest-neighbour coupling on an NVIDIA GB300 (sm_103a).
+ *
+ * The problem is the one stated in Mulansky, "Optimizing Large-Scale ODE Simulations"
+ * (arXiv:1412.0544):
+ *   - Sec. 2.1, Eq. (2): a homogeneous chain r_i' = f(r_i) + g(r_i, r_{i-1}, r_{i+1}) of N
+ *     sites, each a D-dimensional state, stored site after site (Fig. 1: x1 y1 z1 x2 ...);
+ *   - Sec. 2.2, Eqs. (3)-(5): an explicit Runge-Kutta step; here the classical RK4 tableau
+ *     c = (0, 1/2, 1/2, 1), a21 = a32 = 1/2, a43 = 1, b = (1/6, 1/3, 1/3, 1/6), combined as
+ *     y <- y + dt/6 (k1 + 2 k2 + 2 k3 + k4);
+ *   - Sec. 3.1, Eqs. (6)-(7): the coupled Roessler chain (D = 3) with a = 0.2, b = 1, c = 9,
+ *     f = (-y - z, x + a y, b + z (x - c)), g = kappa (x_{i-1} - 2 x_i + x_{i+1}, 0, 0);
+ *     kappa = 1 is the paper's chain;
+ *   - a harmonic chain from the same class (D = 2): q' = p,
+ *     p' = -omega0^2 q + kappa (q_{i-1} - 2 q_i + q_{i+1});
+ *   - Sec. 3.1: periodic ends r_0 = r_N, r_{N+1} = r_1; or fixed ends r_0 = r_{N+1} = 0
+ *     (a Dirichlet reading; the paper only uses periodic ends).
+ * Sec. 2.3's granularity with overlap (a cluster of G sites plus s = 4 sites of halo per side
+ * per step) is realised as temporal blocking: one thread block advances a tile of G sites,
+ * plus 4k halo sites per side, by k steps per launch, redundantly recomputing the halo.
+ *
+ * Conventions for every call:
+ *   - Return value: RK4_OK (0) or a negative RK4_E* code; rk4_strerror() names it.  No C++
+ *     exception crosses this boundary.  A call that fails with RK4_EINVAL enqueues nothing.
+ *   - Device buffers are plain device pointers owned by the caller.  The library never
+ *     allocates device memory; it owns only host-side plan state inside the handle.
+ *   - Work is enqueued on the CUDA stream given at creation (NULL = the legacy default
+ *     stream) and is asynchronous unless the call says it synchronises.
+ *   - State layout: [N][D] site-major ("AoS", Fig. 1), contiguous, FP64 (double) for
+ *     RK4_FP64 or FP32 (float) for RK4_FP32_KAHAN.  For a batch the chains lie back to
+ *     back in the order given at creation.
+ *   - comp: for RK4_FP32_KAHAN, the Kahan compensation of every state component, same
+ *     shape and type as the state, zero before the first step and preserved by the caller
+ *     between calls (it is part of the integrator's state).  NULL for RK4_FP64.
+ *   - ws / ws_bytes: a device workspace of at least rk4_chain_workspace_bytes() bytes,
+ *     256-byte aligned; contents need not be preserved between calls.  It holds the
+ *     ping-pong copy of the state, reduction partials and the device status word.
+ *   - Device-side errors (non-finite values seen by a reduction, a barrier wait that ran
+ *     out of time) are latched in the status word inside ws and reported by
+ *     rk4_chain_status().  Every integrate and energy call clears the status word when it
+ *     starts, so the status describes the most recent such call on that workspace.
+ */
+#ifndef RK4CHAIN_H
+#define RK4CHAIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RK4_OK 0
+#define RK4_EINVAL (-1)        /* bad argument (NULL, N < 1, dt not finite and > 0, ...) */
+#define RK4_ENOMEM_WS (-2)     /* ws_bytes smaller than rk4_chain_workspace_bytes() */
+#define RK4_ECUDA (-3)         /* a CUDA runtime call failed */
+#define RK4_ENONFINITE (-4)    /* a NaN or infinity was found in the state */
+#define RK4_ETIMEOUT (-5)      /* a bounded device-side wait gave up */
+#define RK4_EUNSUPPORTED (-6)  /* valid request this build does not support */
+
+enum rk4_model { RK4_ROESSLER = 0, RK4_HARMONIC = 1 };
+enum rk4_precision { RK4_FP64 = 0, RK4_FP32_KAHAN = 1 };
+enum rk4_bc { RK4_PERIODIC = 0, RK4_FIXED = 1 };
+
+/* Which GPU scheme advances the state.
+ * RK4_KERNEL_STAGED: the paper's "standard implementation" (Sec. 2.2): one launch per RK
+ *   stage, each a full sweep over the chain (4 launches per step).
+ * RK4_KERNEL_BLOCKED: temporal blocking (Sec. 2.3 on the GPU): tiles of G sites plus a halo
+ *   of 4k sites per side advance k steps per launch; k = 1 is the fused single-step kernel.
+ * RK4_KERNEL_PERSISTENT: (batches) one persistent cooperative launch walks the tile list for
+ *   every block of k steps, separated by a bounded-wait grid barrier.
+ * Every scheme performs the same floating-point operations per site, so all give
+ * bit-identical results. */
+enum rk4_kernel { RK4_KERNEL_AUTO = 0, RK4_KERNEL_STAGED = 1, RK4_KERNEL_BLOCKED = 2, RK4_KERNEL_PERSISTENT = 3 };
+
+/* Model parameters.  Defaults (rk4_params_default): a = 0.2, b = 1, c = 9 (Sec. 3.1),
+ * kappa = 1 (Eq. (7) has no coefficient), omega0 = 1. */
+typedef struct {
+  double a, b, c;  /* Roessler f, Eq. (6) */
+  double kappa;    /* coupling strength multiplying g, Eq. (7) */
+  double omega0;   /* harmonic chain on-site frequency */
+} rk4_params;
+
+/* Tiling of the blocked kernels: a tile is block * v sites, of which G = block * v - 8 k are
+ * written back (the rest is the 4k-site halo on each side). */
+typedef struct {
+  int block;  /* threads per block: 64 .. 1024, a multiple of 32 */
+  int v;      /* consecutive sites per thread: 1, 2, 4 or 8 */
+  int k;      /* RK4 steps per launch: 1 .. 16 */
+  int G;      /* output: interior sites per tile */
+} rk4_tiling;
+
+typedef struct rk4_chain rk4_chain; /* opaque host-side handle */
+
+/* Fills *p with the defaults listed above. */
+void rk4_params_default(rk4_params *p);
+
+/* Creates a handle for one chain of n >= 1 sites.  model: enum rk4_model; precision: enum
+ * rk4_precision; bc: enum rk4_bc; dt > 0 and finite; p may be NULL for the defaults;
+ * cuda_stream is a cudaStream_t (NULL = legacy default stream).  On success *out owns the
+ * handle (free it with rk4_chain_destroy).  Errors: RK4_EINVAL. */
+int rk4_chain_create(rk4_chain **out, int model, int precision, int64_t n, double dt, int bc,
+                     const rk4_params *p, void *cuda_stream);
+
+/* Creates a handle for nchains independent chains integrated together (host arrays of
+ * nchains entries, copied): lengths[c] >= 1, kappa[c] replaces p->kappa for chain c,
+ * bc[c] is its boundary.  The state is the chains' [N_c][D] blocks back to back.
+ * Errors: RK4_EINVAL. */
+int rk4_batch_create(rk4_chain **out, int model, int precision, int nchains, const int64_t *lengths,
+                     const double *kappa, const int8_t *bc, double dt, const rk4_params *p,
+                     void *cuda_stream);
+
+/* Bytes of workspace the handle needs for its current kernel choice and tiling. */
+int rk4_chain_workspace_bytes(const rk4_chain *h, size_t *bytes);
+
+/* Total sites (sum over chains) and per-site dimension D of the handle's state. */
+int rk4_chain_shape(const rk4_chain *h, int64_t *total_sites, int *dim);
+
+/* Chooses the scheme (enum rk4_kernel).  AUTO picks BLOCKED for one chain and PERSISTENT
+ * for a batch.  Errors: RK4_EINVAL. */
+int rk4_chain_set_kernel(rk4_chain *h, int kernel);
+
+/* Sets the tiling (block, v, k; G is computed).  block = 0 restores the automatic choice.
+ * Errors: RK4_EINVAL when block, v or k is out of range or G < 8k. */
+int rk4_chain_set_tiling(rk4_chain *h, int block, int v, int k);
+int rk4_chain_get_tiling(const rk4_chain *h, rk4_tiling *out);
+
+/* Times the candidate tilings on the caller's buffers and keeps the fastest (the paper
+ * picks G by a performance study, Sec. 3.2.1).  The call integrates `state` (and comp)
+ * forward by an unspecified number of steps: pass scratch copies.  Synchronises the stream.
+ * *best (may be NULL) receives the chosen tiling.  Errors: RK4_EINVAL, RK4_ENOMEM_WS,
+ * RK4_ECUDA. */
+int rk4_chain_autotune(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_bytes,
+                       int probe_steps, rk4_tiling *best);
+
+/* Advances the state one RK4 step (Eqs. (3)-(5)); equivalent to integrate with nsteps = 1. */
+int rk4_chain_step(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_bytes, double *t);
+
+/* Advances the device state nsteps >= 0 RK4 steps in place (stream-ordered).  If t is not
+ * NULL it receives t0 + n dt, n being the steps taken through this handle so far (no
+ * repeated addition).  Launch sequences of the same shape are replayed from a cached CUDA
+ * graph.  Errors: RK4_EINVAL, RK4_ENOMEM_WS, RK4_ECUDA. */
+int rk4_chain_integrate(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_bytes,
+                        int64_t nsteps, double *t);
+
+/* The same starting from and returning to HOST buffers: copies host_state (and host_comp)
+ * into the device buffers dev_state (dev_comp), integrates, copies the result back and
+ * synchronises the stream.  Pinned host memory gives asynchronous copies. */
+int rk4_chain_integrate_host(rk4_chain *h, void *host_state, void *host_comp, void *dev_state,
+                             void *dev_comp, void *ws, size_t ws_bytes, int64_t nsteps, double *t);
+
+/* FP64 reductions of the state (with the compensation subtracted for RK4_FP32_KAHAN):
+ * RK4_HARMONIC: the energy sum_i (p_i^2/2 + omega0^2 q_i^2/2) + kappa/2 sum_bonds (dq)^2,
+ * including the bonds to the zero ghosts for fixed ends; RK4_ROESSLER: (1/2) sum_i |r_i|^2,
+ * a monitored norm (the Roessler chain is dissipative, not Hamiltonian).  out (host)
+ * receives one value for a single chain, nchains values for a batch.  Synchronises the
+ * stream.  Returns RK4_ENONFINITE if a NaN or infinity was seen. */
+int rk4_chain_energy(rk4_chain *h, const void *state, const void *comp, void *ws, size_t ws_bytes,
+                     double *out);
+
+/* Synchronises the stream, reads and clears the device status word in ws, and returns the
+ * first latched error (RK4_ENONFINITE, RK4_ETIMEOUT) or RK4_OK. */
+int rk4_chain_status(rk4_chain *h, void *ws);
+
+/* Options (enum rk4_option): RK4_OPT_GRAPHS (1 = replay launch sequences from a cached CUDA
+ * graph, the default; 0 = launch directly), RK4_OPT_TIMEOUT_NS (bound on any device-side
+ * barrier wait of the persistent kernel, default 2e9 ns).  Errors: RK4_EINVAL. */
+enum rk4_option { RK4_OPT_GRAPHS = 0, RK4_OPT_TIMEOUT_NS = 1 };
+int rk4_chain_set_option(rk4_chain *h, int option, int64_t value);
+
+/* Test hook for failure detection: runs the persistent kernel for one time block and then
+ * makes its grid barrier wait for one block that never arrives, so that the bounded wait
+ * runs out after timeout_ns and latches RK4_ETIMEOUT in the status word (read it with
+ * rk4_chain_status).  The state is advanced by an unspecified amount: pass scratch buffers.
+ * Needs a batch handle or the persistent kernel.  No GPU fault is involved. */
+int rk4_debug_barrier_timeout(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_bytes,
+                              int64_t timeout_ns);
+
+/* Sets the time origin t0 and resets the step counter. */
+int rk4_chain_set_time(rk4_chain *h, double t0);
+
+/* Frees the handle (and its cached graphs).  NULL is accepted. */
+int rk4_chain_destroy(rk4_chain *h);
+
+/* Static description of an error code. */
+const char *rk4_strerror(int code);
+
+/* Counter-based initial state (SplitMix64, Steele-Lea-Flood 2014): dst[j] for
+ * j = 0 .. count-1 is 2 u - 1 with u = (splitmix64(seed XOR (start + j)) >> 11) * 2^-53, as a
+ * double (exact) or rounded to the nearest float (precision RK4_FP32_KAHAN).  The paper
+ * starts from random initial conditions (Sec. 3.2).  Asynchronous on cuda_stream. */
+int rk4_fill_uniform(void *dst, int64_t count, uint64_t seed, uint64_t start, int precision,
+                     void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RK4CHAIN_H */

@@ -1,0 +1,96 @@
+// k_blocked.cu -- temporally blocked RK4 kernel: one thread block per (chain, tile) item,
+// k steps per launch (k = 1 is the fused single-step kernel).
+#include <mutex>
+
+#include "rk4_tile.cuh"
+
+namespace rk4d {
+
+template <typename R, int MODEL, int V, bool KAHAN>
+__global__ void __launch_bounds__(max_threads_for(V)) k_blocked(BlockedJob job, Coef<R> cf) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int64_t item = blockIdx.x;
+  ChainDesc ch;
+  int64_t tile = item;
+  Coef<R> c = cf;
+  if (job.nchains == 1) {
+    ch = job.one;
+  } else {
+    const int ci = find_chain(job.tile_prefix, job.nchains, item);
+    ch = job.chains[ci];
+    tile = item - job.tile_prefix[ci];
+    c.kappa = (R)ch.kappa;
+  }
+  tile_item<R, MODEL, V, KAHAN, false>(static_cast<const R *>(job.in), static_cast<R *>(job.out),
+                                static_cast<const R *>(job.cin), static_cast<R *>(job.cout), ch, tile, job.K,
+                                job.G, c, smem);
+}
+
+size_t blocked_smem_bytes(int model, bool fp32, int v, int block) {
+  const int D = model == ROESSLER ? 3 : 2;
+  const size_t rs = fp32 ? 4 : 8;
+  return 128 * rs + (size_t)block * v * D * rs * (fp32 ? 2 : 1);
+}
+
+template <typename R, int MODEL, int V, bool KAHAN>
+static cudaError_t launch_one(int block, const BlockedJob &job, const CoefD &cfd, cudaStream_t st) {
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(k_blocked<R, MODEL, V, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    200 * 1024);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  const size_t smem = blocked_smem_bytes(MODEL, KAHAN, V, block);
+  Coef<R> cf = to_coef<R>(cfd, cfd.kappa);
+  if (job.ntiles <= 0) return cudaSuccess;
+  k_blocked<R, MODEL, V, KAHAN><<<(unsigned)job.ntiles, block, smem, st>>>(job, cf);
+  return cudaGetLastError();
+}
+
+template <int MODEL, int V>
+static cudaError_t launch_v(bool fp32, int block, const BlockedJob &job, const CoefD &cf, cudaStream_t st) {
+  return fp32 ? launch_one<float, MODEL, V, true>(block, job, cf, st)
+              : launch_one<double, MODEL, V, false>(block, job, cf, st);
+}
+
+template <int MODEL>
+static cudaError_t launch_m(bool fp32, int v, int block, const BlockedJob &job, const CoefD &cf, cudaStream_t st) {
+  switch (v) {
+    case 1: return launch_v<MODEL, 1>(fp32, block, job, cf, st);
+    case 2: return launch_v<MODEL, 2>(fp32, block, job, cf, st);
+    case 4: return launch_v<MODEL, 4>(fp32, block, job, cf, st);
+    case 8: return launch_v<MODEL, 8>(fp32, block, job, cf, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_blocked(int model, bool fp32, int v, int block, const BlockedJob &job, const CoefD &cf,
+                           cudaStream_t st) {
+  return model == ROESSLER ? launch_m<ROESSLER>(fp32, v, block, job, cf, st)
+                           : launch_m<HARMONIC>(fp32, v, block, job, cf, st);
+}
+
+template <typename R, int MODEL, int V, bool KAHAN>
+static int max_threads_one() {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, k_blocked<R, MODEL, V, KAHAN>) != cudaSuccess) return 0;
+  return a.maxThreadsPerBlock;
+}
+
+template <int MODEL>
+static int max_threads_m(bool fp32, int v) {
+  switch (v) {
+    case 1: return fp32 ? max_threads_one<float, MODEL, 1, true>() : max_threads_one<double, MODEL, 1, false>();
+    case 2: return fp32 ? max_threads_one<float, MODEL, 2, true>() : max_threads_one<double, MODEL, 2, false>();
+    case 4: return fp32 ? max_threads_one<float, MODEL, 4, true>() : max_threads_one<double, MODEL, 4, false>();
+    case 8: return fp32 ? max_threads_one<float, MODEL, 8, true>() : max_threads_one<double, MODEL, 8, false>();
+    default: return 0;
+  }
+}
+
+int blocked_max_threads(int model, bool fp32, int v) {
+  return model == ROESSLER ? max_threads_m<ROESSLER>(fp32, v) : max_threads_m<HARMONIC>(fp32, v);
+}
+
+}  // namespace rk4d

@@ -1,0 +1,162 @@
+// k_persistent.cu -- one persistent, cooperative launch that integrates a whole batch of
+// chains: for every block of k steps each resident thread block walks its share of the
+// (chain, tile) items, then all blocks meet at a grid barrier before the next time block
+// reads what the previous one wrote.  The barrier's wait is bounded: a block that waits
+// longer than timeout_ns latches ST_TIMEOUT in the status word and the kernel returns.
+#include <mutex>
+
+#include "rk4_tile.cuh"
+
+namespace rk4d {
+
+__device__ __forceinline__ long long global_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier over the co-resident blocks of a cooperative launch.  Returns false when
+// this block gave up waiting (or another block already did).
+__device__ __forceinline__ bool grid_barrier(WsHeader *hdr, long long timeout_ns, int extra) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned *gen = &hdr->bar_gen;
+    volatile int *status = &hdr->status;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned expected = gridDim.x + (unsigned)extra;
+    const unsigned arrived = atomicAdd(&hdr->bar_count, 1u) + 1u;
+    if (arrived == expected) {
+      atomicExch(&hdr->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&hdr->bar_gen, 1u);
+    } else {
+      const long long t0 = global_ns();
+      while (*gen == g) {
+        if ((*status & ST_TIMEOUT) || global_ns() - t0 > timeout_ns) {
+          atomicOr(&hdr->status, ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <typename R, int MODEL, int V, bool KAHAN>
+__global__ void __launch_bounds__(max_threads_for(V)) k_persistent(PersistentJob job, Coef<R> cf) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int64_t nblocks_t = job.nmain + job.ntail;
+  for (int64_t t = 0; t < nblocks_t; ++t) {
+    const int ki = (t < job.nmain) ? 0 : job.tail[t - job.nmain];
+    const int K = job.kval[ki];
+    const int G = job.Gval[ki];
+    const int64_t ntiles = job.ntiles[ki];
+    const int32_t *prefix = job.tile_prefix ? job.tile_prefix + (size_t)ki * (job.nchains + 1) : nullptr;
+    const R *in = static_cast<const R *>((t & 1) ? job.bufB : job.bufA);
+    R *out = static_cast<R *>((t & 1) ? job.bufA : job.bufB);
+    const R *cin = static_cast<const R *>((t & 1) ? job.cB : job.cA);
+    R *cout = static_cast<R *>((t & 1) ? job.cA : job.cB);
+    for (int64_t item = blockIdx.x; item < ntiles; item += gridDim.x) {
+      ChainDesc ch;
+      int64_t tile = item;
+      Coef<R> c = cf;
+      if (job.nchains == 1) {
+        ch = job.one;
+      } else {
+        const int ci = find_chain(prefix, job.nchains, item);
+        ch = job.chains[ci];
+        tile = item - prefix[ci];
+        c.kappa = (R)ch.kappa;
+      }
+      tile_item<R, MODEL, V, KAHAN, true>(in, out, cin, cout, ch, tile, K, G, c, smem);
+    }
+    if (t + 1 < nblocks_t || job.extra_arrivals > 0) {
+      if (!grid_barrier(job.hdr, job.timeout_ns, job.extra_arrivals)) return;
+    }
+  }
+}
+
+template <typename R, int MODEL, int V, bool KAHAN>
+static cudaError_t setup_attr() {
+  static std::once_flag once;
+  static cudaError_t err = cudaSuccess;
+  std::call_once(once, [] {
+    err = cudaFuncSetAttribute(k_persistent<R, MODEL, V, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               200 * 1024);
+  });
+  return err;
+}
+
+template <typename R, int MODEL, int V, bool KAHAN>
+static cudaError_t launch_one(int block, int grid, const PersistentJob &job, const CoefD &cfd, cudaStream_t st) {
+  cudaError_t e = setup_attr<R, MODEL, V, KAHAN>();
+  if (e != cudaSuccess) return e;
+  const size_t smem = blocked_smem_bytes(MODEL, KAHAN, V, block);
+  Coef<R> cf = to_coef<R>(cfd, cfd.kappa);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_persistent<R, MODEL, V, KAHAN>, job, cf);
+}
+
+template <typename R, int MODEL, int V, bool KAHAN>
+static int max_grid_one(int block) {
+  if (setup_attr<R, MODEL, V, KAHAN>() != cudaSuccess) return 0;
+  int per_sm = 0;
+  const size_t smem = blocked_smem_bytes(MODEL, KAHAN, V, block);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<R, MODEL, V, KAHAN>, block, smem) !=
+      cudaSuccess)
+    return 0;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return per_sm * sms;
+}
+
+#define RK4_DISPATCH_V(FN, ...)                                                                   \
+  switch (v) {                                                                                     \
+    case 1: return fp32 ? FN<float, MODEL, 1, true>(__VA_ARGS__) : FN<double, MODEL, 1, false>(__VA_ARGS__); \
+    case 2: return fp32 ? FN<float, MODEL, 2, true>(__VA_ARGS__) : FN<double, MODEL, 2, false>(__VA_ARGS__); \
+    case 4: return fp32 ? FN<float, MODEL, 4, true>(__VA_ARGS__) : FN<double, MODEL, 4, false>(__VA_ARGS__); \
+    case 8: return fp32 ? FN<float, MODEL, 8, true>(__VA_ARGS__) : FN<double, MODEL, 8, false>(__VA_ARGS__); \
+    default: break;                                                                                \
+  }
+
+template <int MODEL>
+static cudaError_t launch_m(bool fp32, int v, int block, int grid, const PersistentJob &job, const CoefD &cf,
+                            cudaStream_t st) {
+  RK4_DISPATCH_V(launch_one, block, grid, job, cf, st)
+  return cudaErrorInvalidValue;
+}
+
+template <int MODEL>
+static int max_grid_m(bool fp32, int v, int block) {
+  RK4_DISPATCH_V(max_grid_one, block)
+  return 0;
+}
+
+cudaError_t launch_persistent(int model, bool fp32, int v, int block, int grid, const PersistentJob &job,
+                              const CoefD &cf, cudaStream_t st) {
+  return model == ROESSLER ? launch_m<ROESSLER>(fp32, v, block, grid, job, cf, st)
+                           : launch_m<HARMONIC>(fp32, v, block, grid, job, cf, st);
+}
+
+int persistent_max_grid(int model, bool fp32, int v, int block) {
+  return model == ROESSLER ? max_grid_m<ROESSLER>(fp32, v, block) : max_grid_m<HARMONIC>(fp32, v, block);
+}
+
+}  // namespace rk4d

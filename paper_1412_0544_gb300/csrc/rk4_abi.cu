@@ -1,0 +1,775 @@
+// rk4_abi.cu -- host runtime behind the C ABI of include/rk4chain.h: argument checking,
+// workspace layout, launch plans (k steps per launch, ping-pong buffers), CUDA-graph replay,
+// the tiling autotuner, reductions and the status word.  Only host code lives here; every
+// floating-point operation of the integrator runs in the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/rk4chain.h"
+#include "rk4_internal.h"
+
+using namespace rk4d;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxDistinctK = 4;
+constexpr size_t kMaxSmem = 200 * 1024;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct GraphKey {
+  int kernel = -1;
+  const void *state = nullptr, *comp = nullptr, *ws = nullptr;
+  int64_t nsteps = -1;
+  int block = 0, v = 0, k = 0;
+  long long timeout = 0;
+  bool operator==(const GraphKey &o) const {
+    return kernel == o.kernel && state == o.state && comp == o.comp && ws == o.ws && nsteps == o.nsteps &&
+           block == o.block && v == o.v && k == o.k && timeout == o.timeout;
+  }
+};
+
+struct WsLayout {
+  size_t hdr, partials, result, chains, prefix, state, comp, u0, u1, acc, total;
+};
+
+// One launch plan: the k of every launch (or time block) and whether the result needs copying
+// back from the workspace because the count of ping-pong swaps is odd.
+struct Plan {
+  int64_t nmain = 0;            // launches with kval[0]
+  std::vector<int> tail;        // indices into kval
+  std::vector<int> kval;        // distinct k values, kval[0] = the main k
+  bool copy_back = false;
+  int64_t count() const { return nmain + (int64_t)tail.size(); }
+  int k_at(int64_t i) const { return kval[i < nmain ? 0 : tail[i - nmain]]; }
+};
+
+}  // namespace
+
+struct rk4_chain {
+  int model = 0, precision = 0, D = 3;
+  bool fp32 = false;
+  int nchains = 1;
+  std::vector<ChainDesc> chains;
+  int64_t total = 0;
+  double dt = 0.01;
+  rk4_params p{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int kernel = RK4_KERNEL_AUTO;
+  bool tiling_auto = true;
+  rk4_tiling tiling{};
+  double t0 = 0.0;
+  int64_t nstep = 0;
+  bool graphs = true;
+  long long timeout_ns = 2000000000LL;
+  // pinned host staging: chain table followed by kMaxDistinctK tile-prefix arrays
+  void *h_tables = nullptr;
+  size_t tables_bytes = 0;
+  std::vector<int> tables_k;  // the k values the prefix arrays currently describe
+  int tables_W = 0;           // and the tile width they were computed for
+  double *h_out = nullptr;    // pinned: reduction results (nchains doubles)
+  int *h_status = nullptr;    // pinned: status word read-back
+  GraphKey gkey;
+  cudaGraphExec_t gexec = nullptr;
+};
+
+namespace {
+
+int effective_kernel(const rk4_chain *h) {
+  if (h->kernel != RK4_KERNEL_AUTO) return h->kernel;
+  return h->nchains == 1 ? RK4_KERNEL_BLOCKED : RK4_KERNEL_PERSISTENT;
+}
+
+size_t elem_bytes(const rk4_chain *h) { return h->fp32 ? 4 : 8; }
+
+WsLayout layout(const rk4_chain *h, int kernel) {
+  WsLayout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o = align_up(o + bytes);
+    return r;
+  };
+  L.hdr = take(sizeof(WsHeader));
+  L.partials = take(sizeof(double) * kEnergyBlocks);
+  L.result = take(sizeof(double) * (size_t)h->nchains);
+  L.chains = take(h->nchains > 1 ? sizeof(ChainDesc) * (size_t)h->nchains : 0);
+  L.prefix = take(h->nchains > 1 ? sizeof(int32_t) * (size_t)(h->nchains + 1) * kMaxDistinctK : 0);
+  const size_t sz = (size_t)h->total * (size_t)h->D * elem_bytes(h);
+  L.state = L.comp = L.u0 = L.u1 = L.acc = 0;
+  if (kernel == RK4_KERNEL_STAGED) {
+    L.u0 = take(sz);
+    L.u1 = take(sz);
+    L.acc = take(sz);
+  } else {
+    L.state = take(sz);
+    if (h->fp32) L.comp = take(sz);
+  }
+  L.total = o;
+  return L;
+}
+
+CoefD coef(const rk4_chain *h) {
+  CoefD c;
+  c.a = h->p.a;
+  c.b = h->p.b;
+  c.c = h->p.c;
+  c.kappa = h->p.kappa;
+  c.w2 = h->p.omega0 * h->p.omega0;
+  c.h2 = h->dt / 2.0;
+  c.h1 = h->dt;
+  c.dt6 = h->dt / 6.0;
+  return c;
+}
+
+int tiling_valid(const rk4_chain *h, int block, int v, int k) {
+  if (block < 64 || block > 1024 || (block % 32) != 0) return 0;
+  if (v != 1 && v != 2 && v != 4 && v != 8) return 0;
+  if (k < 1 || k > 16) return 0;
+  const int W = block * v;
+  if (W - 8 * k < 8 * k) return 0;
+  if (blocked_smem_bytes(h->model, h->fp32, v, block) > kMaxSmem) return 0;
+  return 1;
+}
+
+void default_tiling(rk4_chain *h) {
+  // Seed choice from the register and shared-memory budget (the paper suggests sizing the
+  // cluster from the cache; here a tile should fill a block's registers): FP64 is bound by
+  // the FP64 pipe, so k = 1 keeps the redundant halo work minimal; FP32 is bandwidth-bound
+  // at k = 1, so several steps per launch pay off.
+  h->tiling.block = 256;
+  h->tiling.v = 4;
+  h->tiling.k = h->fp32 ? 4 : 1;
+  h->tiling.G = h->tiling.block * h->tiling.v - 8 * h->tiling.k;
+}
+
+int64_t tiles_for(const rk4_chain *h, int G) {
+  int64_t t = 0;
+  for (const ChainDesc &c : h->chains) t += (c.n + G - 1) / G;
+  return t;
+}
+
+Plan make_plan(int64_t nsteps, int K) {
+  Plan P;
+  P.kval.push_back(K);
+  const int64_t q = nsteps / K;
+  const int r = (int)(nsteps % K);
+  auto kidx = [&](int k) {
+    for (size_t i = 0; i < P.kval.size(); ++i)
+      if (P.kval[i] == k) return (int)i;
+    P.kval.push_back(k);
+    return (int)P.kval.size() - 1;
+  };
+  P.nmain = q;
+  if (r > 0) P.tail.push_back(kidx(r));
+  if (P.count() % 2 == 1) {
+    if (r >= 2) {
+      P.tail.clear();
+      P.tail.push_back(kidx(r / 2));
+      P.tail.push_back(kidx(r - r / 2));
+    } else if (K >= 2 && q >= 1) {
+      P.nmain = q - 1;
+      std::vector<int> t;
+      t.push_back(kidx(K / 2));
+      t.push_back(kidx(K - K / 2));
+      for (int x : P.tail) t.push_back(x);
+      P.tail = t;
+    } else {
+      P.copy_back = true;
+    }
+  }
+  return P;
+}
+
+cudaError_t ensure_pinned(rk4_chain *h) {
+  if (!h->h_out) {
+    cudaError_t e = cudaMallocHost((void **)&h->h_out, sizeof(double) * (size_t)h->nchains + 64);
+    if (e != cudaSuccess) return e;
+  }
+  if (!h->h_status) {
+    cudaError_t e = cudaMallocHost((void **)&h->h_status, 64);
+    if (e != cudaSuccess) return e;
+  }
+  if (h->nchains > 1 && !h->h_tables) {
+    // same relative layout as the workspace: chain table, then the prefix arrays at the next
+    // 256-byte boundary
+    h->tables_bytes = align_up(sizeof(ChainDesc) * (size_t)h->nchains) +
+                      sizeof(int32_t) * (size_t)(h->nchains + 1) * kMaxDistinctK;
+    cudaError_t e = cudaMallocHost(&h->h_tables, h->tables_bytes);
+    if (e != cudaSuccess) return e;
+    std::memcpy(h->h_tables, h->chains.data(), sizeof(ChainDesc) * (size_t)h->nchains);
+  }
+  return cudaSuccess;
+}
+
+// Fill the pinned tile-prefix arrays for the plan's k values (waits for earlier uses first).
+cudaError_t prepare_tables(rk4_chain *h, const std::vector<int> &kval, int W) {
+  if (h->nchains == 1) return cudaSuccess;
+  if (h->tables_k == kval && h->tables_W == W) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return e;
+  int32_t *pre = reinterpret_cast<int32_t *>(static_cast<char *>(h->h_tables) +
+                                             align_up(sizeof(ChainDesc) * (size_t)h->nchains));
+  for (size_t i = 0; i < kval.size(); ++i) {
+    const int G = W - 8 * kval[i];
+    int64_t acc = 0;
+    int32_t *p = pre + i * (size_t)(h->nchains + 1);
+    for (int c = 0; c < h->nchains; ++c) {
+      p[c] = (int32_t)acc;
+      acc += (h->chains[c].n + G - 1) / G;
+    }
+    p[h->nchains] = (int32_t)acc;
+  }
+  h->tables_k = kval;
+  h->tables_W = W;
+  return cudaSuccess;
+}
+
+cudaError_t upload_tables(rk4_chain *h, char *ws, const WsLayout &L, cudaStream_t st) {
+  if (h->nchains == 1) return cudaSuccess;
+  return cudaMemcpyAsync(ws + L.chains, h->h_tables, h->tables_bytes, cudaMemcpyHostToDevice, st);
+}
+
+const ChainDesc *dev_chains(const rk4_chain *h, char *ws, const WsLayout &L) {
+  return h->nchains > 1 ? reinterpret_cast<const ChainDesc *>(ws + L.chains) : nullptr;
+}
+
+// Enqueue the whole launch sequence of an integration on stream st.
+cudaError_t enqueue_integrate(rk4_chain *h, int kernel, void *state, void *comp, char *ws, const WsLayout &L,
+                              const Plan &P, int64_t nsteps, cudaStream_t st) {
+  const CoefD cf = coef(h);
+  const int W = h->tiling.block * h->tiling.v;
+  // a fresh status word (and barrier counters) for every integration
+  cudaError_t e = cudaMemsetAsync(ws + L.hdr, 0, sizeof(WsHeader), st);
+  if (e != cudaSuccess) return e;
+  e = upload_tables(h, ws, L, st);
+  if (e != cudaSuccess) return e;
+  const size_t bytes = (size_t)h->total * h->D * elem_bytes(h);
+  if (kernel == RK4_KERNEL_STAGED) {
+    StagedJob j{};
+    j.y = state;
+    j.cmp = comp;
+    j.nchains = h->nchains;
+    j.one = h->chains[0];
+    j.chains = dev_chains(h, ws, L);
+    j.total = h->total;
+    j.acc = ws + L.acc;
+    void *u0 = ws + L.u0, *u1 = ws + L.u1;
+    for (int64_t s = 0; s < nsteps; ++s) {
+      // stage 0 reads y and writes u0; 1: u0 -> u1; 2: u1 -> u0; 3: u0 -> y
+      for (int st4 = 0; st4 < 4; ++st4) {
+        j.uin = (st4 == 2) ? u1 : u0;
+        j.uout = (st4 == 1) ? u1 : u0;
+        e = launch_staged(h->model, h->fp32, st4, j, cf, st);
+        if (e != cudaSuccess) return e;
+      }
+    }
+    return cudaSuccess;
+  }
+  void *wsS = ws + L.state;
+  void *wsC = h->fp32 ? (void *)(ws + L.comp) : nullptr;
+  if (kernel == RK4_KERNEL_BLOCKED) {
+    BlockedJob j{};
+    j.nchains = h->nchains;
+    j.one = h->chains[0];
+    j.chains = dev_chains(h, ws, L);
+    const int32_t *pre = h->nchains > 1 ? reinterpret_cast<const int32_t *>(ws + L.prefix) : nullptr;
+    for (int64_t i = 0; i < P.count(); ++i) {
+      const int k = P.k_at(i);
+      int ki = 0;
+      while (P.kval[ki] != k) ++ki;
+      j.K = k;
+      j.G = W - 8 * k;
+      j.ntiles = tiles_for(h, j.G);
+      j.tile_prefix = pre ? pre + (size_t)ki * (h->nchains + 1) : nullptr;
+      const bool even = (i % 2) == 0;
+      j.in = even ? state : wsS;
+      j.out = even ? wsS : state;
+      j.cin = even ? comp : wsC;
+      j.cout = even ? wsC : comp;
+      e = launch_blocked(h->model, h->fp32, h->tiling.v, h->tiling.block, j, cf, st);
+      if (e != cudaSuccess) return e;
+    }
+  } else {  // persistent
+    PersistentJob j{};
+    j.bufA = state;
+    j.bufB = wsS;
+    j.cA = comp;
+    j.cB = wsC;
+    j.nchains = h->nchains;
+    j.one = h->chains[0];
+    j.chains = dev_chains(h, ws, L);
+    j.tile_prefix = h->nchains > 1 ? reinterpret_cast<const int32_t *>(ws + L.prefix) : nullptr;
+    j.nk = (int)P.kval.size();
+    int64_t maxtiles = 0;
+    for (int i = 0; i < j.nk; ++i) {
+      j.kval[i] = P.kval[i];
+      j.Gval[i] = W - 8 * P.kval[i];
+      j.ntiles[i] = tiles_for(h, j.Gval[i]);
+      maxtiles = std::max(maxtiles, j.ntiles[i]);
+    }
+    j.nmain = P.nmain;
+    j.ntail = (int)P.tail.size();
+    for (int i = 0; i < j.ntail; ++i) j.tail[i] = P.tail[i];
+    j.hdr = reinterpret_cast<WsHeader *>(ws + L.hdr);
+    j.timeout_ns = h->timeout_ns;
+    j.extra_arrivals = 0;
+    int grid = persistent_max_grid(h->model, h->fp32, h->tiling.v, h->tiling.block);
+    if (grid <= 0) return cudaErrorInvalidConfiguration;
+    grid = (int)std::min<int64_t>(grid, std::max<int64_t>(1, maxtiles));
+    e = launch_persistent(h->model, h->fp32, h->tiling.v, h->tiling.block, grid, j, cf, st);
+    if (e != cudaSuccess) return e;
+  }
+  if (P.copy_back) {
+    e = cudaMemcpyAsync(state, wsS, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    if (h->fp32) e = cudaMemcpyAsync(comp, wsC, bytes, cudaMemcpyDeviceToDevice, st);
+  }
+  return e;
+}
+
+int check_buffers(const rk4_chain *h, const void *state, const void *comp, const void *ws) {
+  if (!state || !ws) return RK4_EINVAL;
+  if (h->fp32 != (comp != nullptr)) return RK4_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return RK4_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(state) % 16) != 0) return RK4_EINVAL;
+  if (comp && (reinterpret_cast<uintptr_t>(comp) % 16) != 0) return RK4_EINVAL;
+  return RK4_OK;
+}
+
+int integrate_impl(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_bytes, int64_t nsteps) {
+  int rc = check_buffers(h, state, comp, ws);
+  if (rc) return rc;
+  if (nsteps < 0) return RK4_EINVAL;
+  const int kernel = effective_kernel(h);
+  const WsLayout L = layout(h, kernel);
+  if (ws_bytes < L.total) return RK4_ENOMEM_WS;
+  if (nsteps == 0) return RK4_OK;
+  if (ensure_pinned(h) != cudaSuccess) return RK4_ECUDA;
+  const int K = (kernel == RK4_KERNEL_STAGED) ? 1 : h->tiling.k;
+  const Plan P = make_plan(nsteps, kernel == RK4_KERNEL_STAGED ? 1 : K);
+  if (kernel != RK4_KERNEL_STAGED) {
+    // tile counts must fit a 1-D grid and the int32 prefix tables
+    const int kmax = *std::max_element(P.kval.begin(), P.kval.end());
+    if (tiles_for(h, h->tiling.block * h->tiling.v - 8 * kmax) > 0x7fffffffLL) return RK4_EUNSUPPORTED;
+  }
+  if (prepare_tables(h, P.kval, h->tiling.block * h->tiling.v) != cudaSuccess) return RK4_ECUDA;
+  char *w = static_cast<char *>(ws);
+
+  const bool use_graph = h->graphs && (kernel != RK4_KERNEL_BLOCKED || P.count() > 1);
+  if (!use_graph) {
+    return enqueue_integrate(h, kernel, state, comp, w, L, P, nsteps, h->stream) == cudaSuccess ? RK4_OK
+                                                                                                : RK4_ECUDA;
+  }
+  GraphKey key;
+  key.kernel = kernel;
+  key.state = state;
+  key.comp = comp;
+  key.ws = ws;
+  key.nsteps = nsteps;
+  key.block = h->tiling.block;
+  key.v = h->tiling.v;
+  key.k = h->tiling.k;
+  key.timeout = h->timeout_ns;
+  if (!(h->gexec && key == h->gkey)) {
+    if (h->gexec) {
+      cudaGraphExecDestroy(h->gexec);
+      h->gexec = nullptr;
+    }
+    if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return RK4_ECUDA;
+    if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) return RK4_ECUDA;
+    cudaError_t e = enqueue_integrate(h, kernel, state, comp, w, L, P, nsteps, h->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      return RK4_ECUDA;
+    }
+    e = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      h->gexec = nullptr;
+      return RK4_ECUDA;
+    }
+    h->gkey = key;
+  }
+  return cudaGraphLaunch(h->gexec, h->stream) == cudaSuccess ? RK4_OK : RK4_ECUDA;
+}
+
+int validate_common(int model, int precision, double dt, const rk4_params *p) {
+  if (model != RK4_ROESSLER && model != RK4_HARMONIC) return RK4_EINVAL;
+  if (precision != RK4_FP64 && precision != RK4_FP32_KAHAN) return RK4_EINVAL;
+  if (!(std::isfinite(dt) && dt > 0.0)) return RK4_EINVAL;
+  if (p && !(std::isfinite(p->a) && std::isfinite(p->b) && std::isfinite(p->c) && std::isfinite(p->kappa) &&
+             std::isfinite(p->omega0)))
+    return RK4_EINVAL;
+  return RK4_OK;
+}
+
+rk4_chain *new_handle(int model, int precision, double dt, const rk4_params *p, void *stream) {
+  rk4_chain *h = new (std::nothrow) rk4_chain();
+  if (!h) return nullptr;
+  h->model = model;
+  h->precision = precision;
+  h->fp32 = precision == RK4_FP32_KAHAN;
+  h->D = model == RK4_ROESSLER ? 3 : 2;
+  h->dt = dt;
+  if (p) h->p = *p; else rk4_params_default(&h->p);
+  h->stream = static_cast<cudaStream_t>(stream);
+  default_tiling(h);
+  return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rk4_params_default(rk4_params *p) {
+  if (!p) return;
+  p->a = 0.2;
+  p->b = 1.0;
+  p->c = 9.0;
+  p->kappa = 1.0;
+  p->omega0 = 1.0;
+}
+
+int rk4_chain_create(rk4_chain **out, int model, int precision, int64_t n, double dt, int bc, const rk4_params *p,
+                     void *cuda_stream) {
+  if (!out) return RK4_EINVAL;
+  *out = nullptr;
+  int rc = validate_common(model, precision, dt, p);
+  if (rc) return rc;
+  if (n < 1 || n > ((int64_t)1 << 40)) return RK4_EINVAL;
+  if (bc != RK4_PERIODIC && bc != RK4_FIXED) return RK4_EINVAL;
+  rk4_chain *h = new_handle(model, precision, dt, p, cuda_stream);
+  if (!h) return RK4_EINVAL;
+  ChainDesc c{};
+  c.off = 0;
+  c.n = n;
+  c.kappa = h->p.kappa;
+  c.bc = bc;
+  h->chains.push_back(c);
+  h->nchains = 1;
+  h->total = n;
+  *out = h;
+  return RK4_OK;
+}
+
+int rk4_batch_create(rk4_chain **out, int model, int precision, int nchains, const int64_t *lengths,
+                     const double *kappa, const int8_t *bc, double dt, const rk4_params *p, void *cuda_stream) {
+  if (!out) return RK4_EINVAL;
+  *out = nullptr;
+  int rc = validate_common(model, precision, dt, p);
+  if (rc) return rc;
+  if (nchains < 1 || !lengths || !kappa || !bc) return RK4_EINVAL;
+  int64_t total = 0;
+  for (int c = 0; c < nchains; ++c) {
+    if (lengths[c] < 1 || !std::isfinite(kappa[c]) || (bc[c] != RK4_PERIODIC && bc[c] != RK4_FIXED))
+      return RK4_EINVAL;
+    total += lengths[c];
+    if (total > ((int64_t)1 << 40)) return RK4_EINVAL;
+  }
+  rk4_chain *h = new_handle(model, precision, dt, p, cuda_stream);
+  if (!h) return RK4_EINVAL;
+  int64_t off = 0;
+  for (int c = 0; c < nchains; ++c) {
+    ChainDesc d{};
+    d.off = off;
+    d.n = lengths[c];
+    d.kappa = kappa[c];
+    d.bc = bc[c];
+    h->chains.push_back(d);
+    off += lengths[c];
+  }
+  h->nchains = nchains;
+  h->total = total;
+  *out = h;
+  return RK4_OK;
+}
+
+int rk4_chain_workspace_bytes(const rk4_chain *h, size_t *bytes) {
+  if (!h || !bytes) return RK4_EINVAL;
+  *bytes = layout(h, effective_kernel(h)).total;
+  return RK4_OK;
+}
+
+int rk4_chain_shape(const rk4_chain *h, int64_t *total_sites, int *dim) {
+  if (!h) return RK4_EINVAL;
+  if (total_sites) *total_sites = h->total;
+  if (dim) *dim = h->D;
+  return RK4_OK;
+}
+
+int rk4_chain_set_kernel(rk4_chain *h, int kernel) {
+  if (!h || kernel < RK4_KERNEL_AUTO || kernel > RK4_KERNEL_PERSISTENT) return RK4_EINVAL;
+  h->kernel = kernel;
+  return RK4_OK;
+}
+
+int rk4_chain_set_tiling(rk4_chain *h, int block, int v, int k) {
+  if (!h) return RK4_EINVAL;
+  if (block == 0) {
+    h->tiling_auto = true;
+    default_tiling(h);
+    return RK4_OK;
+  }
+  if (!tiling_valid(h, block, v, k)) return RK4_EINVAL;
+  const int maxt = blocked_max_threads(h->model, h->fp32, v);
+  if (maxt > 0 && block > maxt) return RK4_EINVAL;
+  h->tiling_auto = false;
+  h->tiling.block = block;
+  h->tiling.v = v;
+  h->tiling.k = k;
+  h->tiling.G = block * v - 8 * k;
+  return RK4_OK;
+}
+
+int rk4_chain_get_tiling(const rk4_chain *h, rk4_tiling *out) {
+  if (!h || !out) return RK4_EINVAL;
+  *out = h->tiling;
+  return RK4_OK;
+}
+
+int rk4_chain_integrate(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_bytes, int64_t nsteps, double *t) {
+  if (!h) return RK4_EINVAL;
+  int rc = integrate_impl(h, state, comp, ws, ws_bytes, nsteps);
+  if (rc == RK4_OK) {
+    h->nstep += nsteps;
+    if (t) *t = h->t0 + (double)h->nstep * h->dt;
+  }
+  return rc;
+}
+
+int rk4_chain_step(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_bytes, double *t) {
+  return rk4_chain_integrate(h, state, comp, ws, ws_bytes, 1, t);
+}
+
+int rk4_chain_integrate_host(rk4_chain *h, void *host_state, void *host_comp, void *dev_state, void *dev_comp,
+                             void *ws, size_t ws_bytes, int64_t nsteps, double *t) {
+  if (!h || !host_state) return RK4_EINVAL;
+  if (h->fp32 != (host_comp != nullptr)) return RK4_EINVAL;
+  int rc = check_buffers(h, dev_state, dev_comp, ws);
+  if (rc) return rc;
+  if (ws_bytes < layout(h, effective_kernel(h)).total) return RK4_ENOMEM_WS;
+  const size_t bytes = (size_t)h->total * h->D * elem_bytes(h);
+  if (cudaMemcpyAsync(dev_state, host_state, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) return RK4_ECUDA;
+  if (h->fp32 && cudaMemcpyAsync(dev_comp, host_comp, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return RK4_ECUDA;
+  rc = rk4_chain_integrate(h, dev_state, dev_comp, ws, ws_bytes, nsteps, t);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(host_state, dev_state, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return RK4_ECUDA;
+  if (h->fp32 && cudaMemcpyAsync(host_comp, dev_comp, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return RK4_ECUDA;
+  return cudaStreamSynchronize(h->stream) == cudaSuccess ? RK4_OK : RK4_ECUDA;
+}
+
+int rk4_chain_energy(rk4_chain *h, const void *state, const void *comp, void *ws, size_t ws_bytes, double *out) {
+  if (!h || !out) return RK4_EINVAL;
+  int rc = check_buffers(h, state, comp, ws);
+  if (rc) return rc;
+  const WsLayout L = layout(h, effective_kernel(h));
+  if (ws_bytes < L.total) return RK4_ENOMEM_WS;
+  if (ensure_pinned(h) != cudaSuccess) return RK4_ECUDA;
+  char *w = static_cast<char *>(ws);
+  WsHeader *hdr = reinterpret_cast<WsHeader *>(w + L.hdr);
+  if (cudaMemsetAsync(hdr, 0, sizeof(WsHeader), h->stream) != cudaSuccess) return RK4_ECUDA;
+  if (upload_tables(h, w, L, h->stream) != cudaSuccess) return RK4_ECUDA;
+  const CoefD cf = coef(h);
+  double *res = reinterpret_cast<double *>(w + L.result);
+  if (launch_energy(h->model, h->fp32, state, comp, h->nchains, h->chains[0], dev_chains(h, w, L), cf,
+                    reinterpret_cast<double *>(w + L.partials), res, hdr, h->stream) != cudaSuccess)
+    return RK4_ECUDA;
+  if (cudaMemcpyAsync(h->h_out, res, sizeof(double) * h->nchains, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return RK4_ECUDA;
+  if (cudaMemcpyAsync(h->h_status, &hdr->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return RK4_ECUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return RK4_ECUDA;
+  std::memcpy(out, h->h_out, sizeof(double) * h->nchains);
+  if (*h->h_status & ST_NONFINITE) return RK4_ENONFINITE;
+  return RK4_OK;
+}
+
+int rk4_chain_status(rk4_chain *h, void *ws) {
+  if (!h || !ws) return RK4_EINVAL;
+  if (ensure_pinned(h) != cudaSuccess) return RK4_ECUDA;
+  const WsLayout L = layout(h, effective_kernel(h));
+  WsHeader *hdr = reinterpret_cast<WsHeader *>(static_cast<char *>(ws) + L.hdr);
+  if (cudaMemcpyAsync(h->h_status, &hdr->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return RK4_ECUDA;
+  if (cudaMemsetAsync(&hdr->status, 0, sizeof(int), h->stream) != cudaSuccess) return RK4_ECUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return RK4_ECUDA;
+  const int s = *h->h_status;
+  if (s & ST_TIMEOUT) return RK4_ETIMEOUT;
+  if (s & ST_NONFINITE) return RK4_ENONFINITE;
+  return RK4_OK;
+}
+
+int rk4_chain_set_option(rk4_chain *h, int option, int64_t value) {
+  if (!h) return RK4_EINVAL;
+  if (option == RK4_OPT_GRAPHS) {
+    if (value != 0 && value != 1) return RK4_EINVAL;
+    h->graphs = value != 0;
+    return RK4_OK;
+  }
+  if (option == RK4_OPT_TIMEOUT_NS) {
+    if (value < 1000 || value > (int64_t)600 * 1000000000LL) return RK4_EINVAL;
+    h->timeout_ns = value;
+    return RK4_OK;
+  }
+  return RK4_EINVAL;
+}
+
+int rk4_debug_barrier_timeout(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_bytes, int64_t timeout_ns) {
+  if (!h) return RK4_EINVAL;
+  int rc = check_buffers(h, state, comp, ws);
+  if (rc) return rc;
+  if (timeout_ns < 1000 || timeout_ns > 10LL * 1000000000LL) return RK4_EINVAL;
+  const WsLayout L = layout(h, RK4_KERNEL_PERSISTENT);
+  if (ws_bytes < L.total) return RK4_ENOMEM_WS;
+  if (ensure_pinned(h) != cudaSuccess) return RK4_ECUDA;
+  const Plan P = make_plan(h->tiling.k, h->tiling.k);  // one time block
+  const int W = h->tiling.block * h->tiling.v;
+  if (prepare_tables(h, P.kval, W) != cudaSuccess) return RK4_ECUDA;
+  char *w = static_cast<char *>(ws);
+  if (upload_tables(h, w, L, h->stream) != cudaSuccess) return RK4_ECUDA;
+  PersistentJob j{};
+  j.bufA = state;
+  j.bufB = w + L.state;
+  j.cA = comp;
+  j.cB = h->fp32 ? (void *)(w + L.comp) : nullptr;
+  j.nchains = h->nchains;
+  j.one = h->chains[0];
+  j.chains = dev_chains(h, w, L);
+  j.tile_prefix = h->nchains > 1 ? reinterpret_cast<const int32_t *>(w + L.prefix) : nullptr;
+  j.nk = 1;
+  j.kval[0] = h->tiling.k;
+  j.Gval[0] = W - 8 * h->tiling.k;
+  j.ntiles[0] = tiles_for(h, j.Gval[0]);
+  j.nmain = 1;
+  j.ntail = 0;
+  j.hdr = reinterpret_cast<WsHeader *>(w + L.hdr);
+  j.timeout_ns = timeout_ns;
+  j.extra_arrivals = 1;
+  int grid = persistent_max_grid(h->model, h->fp32, h->tiling.v, h->tiling.block);
+  if (grid <= 0) return RK4_ECUDA;
+  grid = (int)std::min<int64_t>(grid, std::max<int64_t>(1, j.ntiles[0]));
+  if (cudaMemsetAsync(w + L.hdr, 0, sizeof(WsHeader), h->stream) != cudaSuccess) return RK4_ECUDA;
+  if (launch_persistent(h->model, h->fp32, h->tiling.v, h->tiling.block, grid, j, coef(h), h->stream) !=
+      cudaSuccess)
+    return RK4_ECUDA;
+  return RK4_OK;
+}
+
+int rk4_chain_autotune(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_bytes, int probe_steps,
+                       rk4_tiling *best) {
+  if (!h || probe_steps < 1 || probe_steps > 100000) return RK4_EINVAL;
+  int rc = check_buffers(h, state, comp, ws);
+  if (rc) return rc;
+  const int kernel = effective_kernel(h);
+  if (kernel == RK4_KERNEL_STAGED) {
+    if (best) *best = h->tiling;
+    return RK4_OK;
+  }
+  if (ws_bytes < layout(h, kernel).total) return RK4_ENOMEM_WS;
+  const rk4_tiling saved = h->tiling;
+  const bool saved_graphs = h->graphs;
+  h->graphs = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    h->graphs = saved_graphs;
+    return RK4_ECUDA;
+  }
+  static const int blocks[] = {128, 256, 512, 1024};
+  static const int vs[] = {1, 2, 4, 8};
+  static const int ks[] = {1, 2, 4, 8, 16};
+  float best_ms = 1e30f;
+  rk4_tiling best_t = saved;
+  rc = RK4_OK;
+  for (int b : blocks)
+    for (int v : vs)
+      for (int k : ks) {
+        if (!tiling_valid(h, b, v, k)) continue;
+        const int maxt = blocked_max_threads(h->model, h->fp32, v);
+        if (maxt <= 0 || b > maxt) continue;
+        if (kernel == RK4_KERNEL_PERSISTENT && persistent_max_grid(h->model, h->fp32, v, b) <= 0) continue;
+        h->tiling.block = b;
+        h->tiling.v = v;
+        h->tiling.k = k;
+        h->tiling.G = b * v - 8 * k;
+        const int64_t steps = ((probe_steps + 2 * k - 1) / (2 * k)) * 2 * k;  // whole, even launch count
+        if (integrate_impl(h, state, comp, ws, ws_bytes, 2 * k) != RK4_OK) continue;  // warm-up
+        cudaEventRecord(e0, h->stream);
+        if (integrate_impl(h, state, comp, ws, ws_bytes, steps) != RK4_OK) continue;
+        cudaEventRecord(e1, h->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          rc = RK4_ECUDA;
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const float per_step = ms / (float)steps;
+        if (per_step < best_ms) {
+          best_ms = per_step;
+          best_t = h->tiling;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->graphs = saved_graphs;
+  if (rc != RK4_OK || best_ms >= 1e30f) {
+    h->tiling = saved;
+    return rc != RK4_OK ? rc : RK4_ECUDA;
+  }
+  h->tiling = best_t;
+  h->tiling_auto = false;
+  if (best) *best = best_t;
+  return RK4_OK;
+}
+
+int rk4_chain_set_time(rk4_chain *h, double t0) {
+  if (!h || !std::isfinite(t0)) return RK4_EINVAL;
+  h->t0 = t0;
+  h->nstep = 0;
+  return RK4_OK;
+}
+
+int rk4_chain_destroy(rk4_chain *h) {
+  if (!h) return RK4_OK;
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->h_tables) cudaFreeHost(h->h_tables);
+  if (h->h_out) cudaFreeHost(h->h_out);
+  if (h->h_status) cudaFreeHost(h->h_status);
+  delete h;
+  return RK4_OK;
+}
+
+const char *rk4_strerror(int code) {
+  switch (code) {
+    case RK4_OK: return "ok";
+    case RK4_EINVAL: return "invalid argument";
+    case RK4_ENOMEM_WS: return "workspace too small";
+    case RK4_ECUDA: return "CUDA runtime error";
+    case RK4_ENONFINITE: return "non-finite value in the state";
+    case RK4_ETIMEOUT: return "device-side wait timed out";
+    case RK4_EUNSUPPORTED: return "unsupported request";
+    default: return "unknown error";
+  }
+}
+
+int rk4_fill_uniform(void *dst, int64_t count, uint64_t seed, uint64_t start, int precision, void *cuda_stream) {
+  if (!dst || count < 0) return RK4_EINVAL;
+  if (precision != RK4_FP64 && precision != RK4_FP32_KAHAN) return RK4_EINVAL;
+  return launch_fill_uniform(dst, count, seed, start, precision == RK4_FP32_KAHAN,
+                             static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess
+             ? RK4_OK
+             : RK4_ECUDA;
+}
+
+}  // extern "C"

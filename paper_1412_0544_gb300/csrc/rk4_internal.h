@@ -1,0 +1,100 @@
+// rk4_internal.h -- structures shared by the host runtime and the kernels' launchers.
+// Not part of the public ABI (see include/rk4chain.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace rk4d {
+
+// One chain of a (possibly single-chain) job.  32 bytes, stored in the workspace for batches.
+struct ChainDesc {
+  int64_t off;   // first site of the chain in the concatenated state
+  int64_t n;     // sites
+  double kappa;  // coupling strength
+  int32_t bc;    // PERIODIC or FIXED
+  int32_t pad;
+};
+
+// Coefficients in double; converted to the working precision once per launch on the host.
+struct CoefD {
+  double a, b, c, kappa, w2, h2, h1, dt6;
+};
+
+// Device status word bits (in the workspace header).
+enum : int { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
+
+// Workspace header: status word, grid-barrier counters.  256 bytes.
+struct WsHeader {
+  int status;
+  unsigned bar_count;
+  unsigned bar_gen;
+  int timeout_where;
+  unsigned char pad[240];
+};
+
+// Arguments of one blocked launch (one chain, or a batch through a chain table).
+struct BlockedJob {
+  const void *in;    // state read by this launch
+  void *out;         // state written by this launch
+  const void *cin;   // Kahan compensation read (FP32) or NULL
+  void *cout;        // Kahan compensation written
+  int nchains;       // 1: use `one`; >1: use `chains` / `tile_prefix`
+  ChainDesc one;
+  const ChainDesc *chains;      // device table (batches)
+  const int32_t *tile_prefix;   // device, nchains + 1 entries: first tile of each chain
+  int K;                        // steps in this launch
+  int G;                        // interior sites per tile
+  int64_t ntiles;               // tiles in the launch
+};
+
+struct StagedJob {
+  void *y;            // state, updated in place at the last stage
+  void *cmp;          // Kahan compensation (FP32) or NULL, updated in place
+  const void *uin;    // stage state read (stages 1..3)
+  void *uout;         // stage state written (stages 0..2)
+  void *acc;          // slope sum
+  int nchains;
+  ChainDesc one;
+  const ChainDesc *chains;   // device table for batches (site -> chain by binary search)
+  int64_t total;             // total sites
+};
+
+struct PersistentJob {
+  void *bufA, *bufB;            // state ping-pong: time block t reads A when t is even
+  void *cA, *cB;                // compensation ping-pong (FP32) or NULL
+  int nchains;
+  ChainDesc one;
+  const ChainDesc *chains;
+  const int32_t *tile_prefix;   // nk arrays of (nchains + 1) entries: first tile of each chain
+  int nk;                       // distinct k values (1..4)
+  int kval[4];                  // steps per time block
+  int Gval[4];                  // interior sites per tile for each k
+  int64_t ntiles[4];            // tiles per time block for each k
+  int64_t nmain;                // leading time blocks that use kval[0]
+  int ntail;                    // trailing time blocks (0..3)
+  int tail[3];                  // their indices into kval
+  WsHeader *hdr;                // status word and barrier counters (zeroed before launch)
+  long long timeout_ns;         // bound on any single barrier wait
+  int extra_arrivals;           // test hook: barrier waits for this many blocks that never come
+};
+
+// Launchers (return a cudaError_t).  R is selected by `fp32` (FP32 + Kahan) or double.
+cudaError_t launch_blocked(int model, bool fp32, int v, int block, const BlockedJob &job, const CoefD &cf,
+                           cudaStream_t st);
+cudaError_t launch_staged(int model, bool fp32, int stage, const StagedJob &job, const CoefD &cf,
+                          cudaStream_t st);
+cudaError_t launch_persistent(int model, bool fp32, int v, int block, int grid, const PersistentJob &job,
+                              const CoefD &cf, cudaStream_t st);
+int persistent_max_grid(int model, bool fp32, int v, int block);
+cudaError_t launch_energy(int model, bool fp32, const void *state, const void *cmp, int nchains,
+                          const ChainDesc &one, const ChainDesc *chains, const CoefD &cf, double *partials,
+                          double *out, WsHeader *hdr, cudaStream_t st);
+cudaError_t launch_fill_uniform(void *dst, int64_t count, uint64_t seed, uint64_t start, bool fp32,
+                                cudaStream_t st);
+size_t blocked_smem_bytes(int model, bool fp32, int v, int block);
+int blocked_max_threads(int model, bool fp32, int v);
+
+constexpr int kEnergyBlocks = 1024;  // fixed grid of the single-chain reduction (deterministic)
+
+}  // namespace rk4d

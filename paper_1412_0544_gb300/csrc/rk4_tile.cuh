@@ -1,0 +1,201 @@
+// rk4_tile.cuh -- temporal blocking of one tile (Sec. 2.3 of the paper, on the GPU).
+//
+// A thread block owns a tile of W = blockDim.x * V consecutive sites of one chain: the G
+// interior sites it will write back plus a halo of H = 4k sites on each side.  Thread t holds
+// sites t*V .. t*V+V-1 in registers.  Every RK stage needs the coupling coordinate of both
+// neighbours: inside a thread it is a register, across lanes a warp shuffle, across warps a
+// two-slot exchange in shared memory (one __syncthreads per stage).  Sites at the tile's
+// ends read a stand-in value, so after m stages only sites [m, W - m) are exact -- the
+// paper's observation that the error from the missing coupling moves one site inward per
+// stage -- and after 4k stages exactly the interior [4k, W - 4k) is.
+//
+// Fixed ends: sites of the tile outside the chain are ghosts whose coupling coordinate is
+// forced to zero at every stage (r_0 = r_{N+1} = 0).  Periodic ends: the tile is a window of
+// the periodically extended chain (indices taken mod N), so no special case is needed.
+#pragma once
+#include "rk4_device.cuh"
+#include "rk4_internal.h"
+
+namespace rk4d {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Largest block the tile kernels are compiled for, by sites per thread: the register budget
+// (about 9 values per site plus temporaries) must fit 65536 registers per block.
+__host__ __device__ constexpr int max_threads_for(int v) { return v <= 1 ? 1024 : (v <= 4 ? 512 : 256); }
+
+// Advance the registers of one tile by K steps.  `edge` is 4 * 32 values of shared memory.
+template <typename R, int MODEL, int V, bool KAHAN, bool MASK>
+__device__ __forceinline__ void tile_advance(R (&y)[V][Dim<MODEL>::D], R (&cmp)[V][Dim<MODEL>::D],
+                                             uint32_t ghost, int K, const Coef<R> &cf, R *edge) {
+  constexpr int D = Dim<MODEL>::D;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  R u[V][D], acc[V][D];
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int d = 0; d < D; ++d) u[v][d] = y[v][d];
+
+#pragma unroll 1
+  for (int s = 0; s < K; ++s) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      R xs[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) xs[v] = (MASK && ((ghost >> v) & 1u)) ? R(0) : u[v][0];
+      R left = __shfl_up_sync(kFull, xs[V - 1], 1);
+      R right = __shfl_down_sync(kFull, xs[0], 1);
+      R *eb = edge + (j & 1) * 64;  // [0,32): first x of each warp, [32,64): last x
+      if (lane == 0) eb[warp] = xs[0];
+      if (lane == 31) eb[32 + warp] = xs[V - 1];
+      __syncthreads();
+      if (lane == 0) left = (warp > 0) ? eb[32 + warp - 1] : xs[0];
+      if (lane == 31) right = (warp < nw - 1) ? eb[warp + 1] : xs[V - 1];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const R xl = (v == 0) ? left : xs[v - 1];
+        const R xr = (v == V - 1) ? right : xs[v + 1];
+        R k[D];
+        slope<R, MODEL>(u[v], xl, xr, cf, k);
+        stage_update<R, D, KAHAN>(j, k, y[v], u[v], acc[v], cmp[v], cf);
+      }
+    }
+  }
+}
+
+// Global loads: the read-only path for one-shot launches; L2-coherent loads (bypassing L1)
+// inside the persistent kernel, whose buffers are rewritten by other blocks between barriers.
+template <bool COH, typename T> __device__ __forceinline__ T gld(const T *p) {
+  if constexpr (COH) return __ldcg(p); else return __ldg(p);
+}
+
+// Copy the W sites starting at chain index t0 (may be negative or run past the end) of the
+// chain at `off` into shared memory, element by element, coalesced.  Periodic: wrapped;
+// fixed: zero outside the chain.
+template <typename R, int D, bool COH>
+__device__ __forceinline__ void tile_load(R *tile, const R *__restrict__ src, int64_t off, int64_t n, int bc,
+                                          int64_t t0, int W) {
+  const int total = W * D;
+  if (t0 >= 0 && t0 + W <= n) {
+    const R *s = src + (off + t0) * D;
+    if ((reinterpret_cast<uintptr_t>(s) & 15u) == 0 && ((total * (int)sizeof(R)) & 15) == 0) {
+      const int nv = total * (int)sizeof(R) / 16;
+      const int4 *s4 = reinterpret_cast<const int4 *>(s);
+      int4 *t4 = reinterpret_cast<int4 *>(tile);
+      for (int e = threadIdx.x; e < nv; e += blockDim.x) t4[e] = gld<COH>(s4 + e);
+    } else {
+      for (int e = threadIdx.x; e < total; e += blockDim.x) tile[e] = gld<COH>(s + e);
+    }
+  } else {
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      const int sl = e / D;
+      const int d = e - sl * D;
+      const int64_t g = t0 + sl;
+      R val;
+      if (bc == PERIODIC) {
+        val = gld<COH>(src + (off + wrap(g, n)) * D + d);
+      } else {
+        val = (g >= 0 && g < n) ? gld<COH>(src + (off + g) * D + d) : R(0);
+      }
+      tile[e] = val;
+    }
+  }
+}
+
+// Store `cnt` sites of the tile starting at tile-local site `first` to chain index g0.
+template <typename R, int D>
+__device__ __forceinline__ void tile_store(R *__restrict__ dst, const R *tile, int64_t off, int first, int64_t g0,
+                                           int cnt) {
+  const int total = cnt * D;
+  R *d0 = dst + (off + g0) * D;
+  const R *s0 = tile + first * D;
+  if ((reinterpret_cast<uintptr_t>(d0) & 15u) == 0 && (reinterpret_cast<uintptr_t>(s0) & 15u) == 0 &&
+      ((total * (int)sizeof(R)) & 15) == 0) {
+    const int nv = total * (int)sizeof(R) / 16;
+    int4 *d4 = reinterpret_cast<int4 *>(d0);
+    const int4 *s4 = reinterpret_cast<const int4 *>(s0);
+    for (int e = threadIdx.x; e < nv; e += blockDim.x) d4[e] = s4[e];
+  } else {
+    for (int e = threadIdx.x; e < total; e += blockDim.x) d0[e] = s0[e];
+  }
+}
+
+// Process one (chain, tile) item end to end: load, advance K steps, store the interior.
+// Shared memory: edge[128] | tile[W*D] | ctile[W*D] (Kahan).
+template <typename R, int MODEL, int V, bool KAHAN, bool COH>
+__device__ __forceinline__ void tile_item(const R *__restrict__ in, R *__restrict__ out, const R *__restrict__ cin,
+                                          R *__restrict__ cout, const ChainDesc &ch, int64_t tile, int K, int G,
+                                          const Coef<R> &cf, unsigned char *smem) {
+  constexpr int D = Dim<MODEL>::D;
+  R *edge = reinterpret_cast<R *>(smem);
+  R *tl = edge + 128;
+  const int W = blockDim.x * V;
+  R *ctl = tl + W * D;
+  const int H = 4 * K;
+  const int64_t t0 = tile * (int64_t)G - H;
+
+  tile_load<R, D, COH>(tl, in, ch.off, ch.n, ch.bc, t0, W);
+  if constexpr (KAHAN) tile_load<R, D, COH>(ctl, cin, ch.off, ch.n, ch.bc, t0, W);
+  __syncthreads();
+
+  R y[V][D], cmp[V][D];
+  const int base = threadIdx.x * V;
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      y[v][d] = tl[(base + v) * D + d];
+      if constexpr (KAHAN) cmp[v][d] = ctl[(base + v) * D + d]; else cmp[v][d] = R(0);
+    }
+
+  const bool edge_tile = (ch.bc == FIXED) && (t0 < 0 || t0 + W > ch.n);
+  if (edge_tile) {
+    uint32_t ghost = 0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int64_t g = t0 + base + v;
+      if (g < 0 || g >= ch.n) ghost |= 1u << v;
+    }
+    tile_advance<R, MODEL, V, KAHAN, true>(y, cmp, ghost, K, cf, edge);
+  } else {
+    tile_advance<R, MODEL, V, KAHAN, false>(y, cmp, 0u, K, cf, edge);
+  }
+
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      tl[(base + v) * D + d] = y[v][d];
+      if constexpr (KAHAN) ctl[(base + v) * D + d] = cmp[v][d];
+    }
+  __syncthreads();
+  const int64_t g0 = t0 + H;  // = tile * G
+  const int64_t rem = ch.n - g0;
+  const int cnt = (int)(rem < G ? rem : G);
+  if (cnt > 0) {
+    tile_store<R, D>(out, tl, ch.off, H, g0, cnt);
+    if constexpr (KAHAN) tile_store<R, D>(cout, ctl, ch.off, H, g0, cnt);
+  }
+  __syncthreads();  // shared memory is reused by the next item
+}
+
+// Locate the chain of a tile index through the prefix array (first tile of each chain).
+__device__ __forceinline__ int find_chain(const int32_t *prefix, int nchains, int64_t tile) {
+  int lo = 0, hi = nchains - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename R> __host__ __device__ inline Coef<R> to_coef(const CoefD &c, double kappa) {
+  Coef<R> r;
+  r.a = (R)c.a; r.b = (R)c.b; r.c = (R)c.c; r.kappa = (R)kappa; r.w2 = (R)c.w2;
+  r.h2 = (R)c.h2; r.h1 = (R)c.h1; r.dt6 = (R)c.dt6;
+  return r;
+}
+
+}  // namespace rk4d
