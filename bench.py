@@ -43,9 +43,10 @@ FP64_INST_PEAK = 0.599e12
 FP32_INST_PEAK = 36.6e12
 FP64_INST_PER_SITE_STEP = 49     # 4 x 7 slope + 9 stage + 9 sum + 3 update
 FP32K_INST_PER_SITE_STEP = 61    # + 4 per component for the Kahan update
-# DRAM traffic per launch of the FP64 blocked kernel from an ncu capture, valid only for the
-# kernel sources whose hash is recorded next to it (else reported as null).
-TRAFFIC = {}
+# DRAM traffic (read + write bytes) per launch of the FP64 blocked kernel at N = 2^24 from an
+# ncu capture (profiles/k_blocked_fp64_roessler_N2e24_full.md), valid only for the kernel
+# sources whose hash and the tiling recorded with it (else reported as null).
+TRAFFIC = {("af03096fd02523bc", "256,4,2"): 403284992 + 357414912}
 
 
 def kernel_hash() -> str:
@@ -285,7 +286,7 @@ def main():
     sps_k = n * NSTEPS * reps / el_k
     achieved_inst = sps_k * FP64_INST_PER_SITE_STEP / 1e9  # G FP64 instructions/s
     khash = kernel_hash()
-    traffic = TRAFFIC.get(khash)
+    traffic = TRAFFIC.get((khash, f"{tiling['block']},{tiling['v']},{tiling['k']}"))
     roofline = {"bound": "alu", "achieved": achieved_inst, "peak": FP64_INST_PEAK / 1e9,
                 "unit": "G FP64 inst/s", "frac": achieved_inst * 1e9 / FP64_INST_PEAK,
                 "traffic": traffic, "kernel": "k_blocked<double, Roessler>",
