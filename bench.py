@@ -37,15 +37,15 @@ DT = 0.01
 SEED = 0x14120544
 D = 3
 HBM_GBS_FALLBACK = 6800.0
-# FP64 pipe rate measured on this GPU model with a dependent-free DFMA loop
-# (profiles/gb300_probe_pipes.md): 0.599e12 FP64 FMA instructions per second.
+# FP64 pipe rate measured on this GPU model with independent DFMA chains (8 per thread, 4-8
+# blocks of 256 threads per SM): 0.599e12 FP64 FMA instructions per second; FP32: 36.6e12.
 FP64_INST_PEAK = 0.599e12
 FP32_INST_PEAK = 36.6e12
 FP64_INST_PER_SITE_STEP = 49     # 4 x 7 slope + 9 stage + 9 sum + 3 update
 FP32K_INST_PER_SITE_STEP = 61    # + 4 per component for the Kahan update
-# DRAM traffic (read + write bytes) per launch of the FP64 blocked kernel at N = 2^24 from an
-# ncu capture (profiles/k_blocked_fp64_roessler_N2e24_full.md), valid only for the kernel
-# sources whose hash and the tiling recorded with it (else reported as null).
+# DRAM traffic (read + write bytes) per launch of the FP64 blocked kernel at N = 2^24 from one
+# ncu --set full capture, valid only for the kernel sources (hash) and the tiling recorded with
+# it; any other combination reports null.
 TRAFFIC = {("af03096fd02523bc", "256,4,2"): 403284992 + 357414912}
 
 
