@@ -159,6 +159,20 @@ int rk4_chain_integrate_host(rk4_chain *h, void *host_state, void *host_comp, vo
 int rk4_chain_energy(rk4_chain *h, const void *state, const void *comp, void *ws, size_t ws_bytes,
                      double *out);
 
+/* The same reduction without a workspace, for callers that cannot allocate device memory --
+ * code that runs where cudaMalloc is not allowed or not reachable (a host callback or hook, a
+ * plug-in whose host application owns all device allocations), so it cannot provide ws.  The
+ * paper has no counterpart: this is a library convenience.  Scratch space (partial sums, one
+ * result per chain, the batch chain table, a status word) is a fixed array compiled into the
+ * library, about 330 KB on every GPU that loads it, held until the process exits; batches
+ * of more than 8192 chains are rejected with RK4_EINVAL.  The call allocates nothing (no
+ * cudaMalloc, cudaMallocHost or cudaFree).  The first call on each device looks up the
+ * array's device address, so make that first call before any stream capture.  All calls
+ * share the array: calls whose work overlaps on the GPU race and must be serialised by the
+ * caller.  out (host) receives one value per chain.  Synchronises the stream.  Returns
+ * RK4_ENONFINITE if a NaN or infinity was seen, RK4_EINVAL for bad arguments. */
+int rk4_chain_energy_static(rk4_chain *h, const void *state, const void *comp, double *out);
+
 /* Synchronises the stream, reads and clears the device status word in ws, and returns the
  * first latched error (RK4_ENONFINITE, RK4_ETIMEOUT) or RK4_OK. */
 int rk4_chain_status(rk4_chain *h, void *ws);

@@ -65,6 +65,7 @@ def _load():
         "rk4_chain_integrate": (c_int, [H, vp, vp, vp, sz, i64, dp]),
         "rk4_chain_integrate_host": (c_int, [H, vp, vp, vp, vp, vp, sz, i64, dp]),
         "rk4_chain_energy": (c_int, [H, vp, vp, vp, sz, dp]),
+        "rk4_chain_energy_static": (c_int, [H, vp, vp, dp]),
         "rk4_chain_status": (c_int, [H, vp]),
         "rk4_chain_set_option": (c_int, [H, c_int, i64]),
         "rk4_debug_barrier_timeout": (c_int, [H, vp, vp, vp, sz, i64]),
@@ -245,6 +246,15 @@ def rk4_chain_energy(h, state, comp, ws, ws_bytes: int | None = None) -> np.ndar
     wb = _nbytes(ws) if ws_bytes is None else ws_bytes
     _check(_lib.rk4_chain_energy(h, _ptr(state), _ptr(comp), _ptr(ws), wb,
                                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "rk4_chain_energy")
+    return out
+
+
+def rk4_chain_energy_static(h, state, comp) -> np.ndarray:
+    """rk4_chain_energy without a workspace (scratch compiled into the library; for callers
+    that cannot allocate device memory).  One value per chain."""
+    out = np.zeros(max(_nchains(h), 1), dtype=np.float64)
+    _check(_lib.rk4_chain_energy_static(h, _ptr(state), _ptr(comp), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+           "rk4_chain_energy_static")
     return out
 
 

@@ -1,0 +1,85 @@
+// k_energy_static.cu -- the FP64 energy / norm reduction for callers that cannot allocate
+// device memory (for example code running where cudaMalloc is forbidden or unavailable: inside
+// a host callback, a signal-safe monitoring hook, or an embedding that hands the library no
+// workspace).  The reduction's scratch -- block partial sums, per-chain results, the batch
+// chain table and the status word -- lives in one file-scope __device__ array instead of the
+// caller's workspace.
+//
+// The array holds kStaticMaxChains chains' worth of scratch (about 330 KB) and stays resident
+// on every GPU that loads this library until the process exits.  All calls share it: two
+// calls whose work overlaps on the GPU (different streams, or different host threads on one
+// device) race on it and must be serialised by the caller.  Each call clears the status word
+// before use; everything else it reads is fully rewritten first.
+#include <mutex>
+
+#include "../../include/rk4chain.h"
+#include "rk4_internal.h"
+
+using namespace rk4d;
+
+namespace {
+
+constexpr int kStaticMaxChains = 8192;
+constexpr int kMaxDevices = 64;
+
+struct StaticScratch {
+  WsHeader hdr;
+  double partials[kEnergyBlocks];
+  double result[kStaticMaxChains];
+  ChainDesc chains[kStaticMaxChains];
+};
+
+// Host code must not pass this symbol to a kernel: on the host it is only a stand-in whose
+// device address comes from cudaGetSymbolAddress (see scratch_for_current_device).
+static __device__ __align__(256) unsigned char g_energy_scratch[sizeof(StaticScratch)];
+
+std::mutex g_mu;
+StaticScratch *g_dev_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once per device.
+cudaError_t scratch_for_current_device(StaticScratch **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_dev_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_energy_scratch);
+    if (e != cudaSuccess) return e;
+    g_dev_ptr[dev] = static_cast<StaticScratch *>(p);
+  }
+  *out = g_dev_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int rk4_chain_energy_static(rk4_chain *h, const void *state, const void *comp, double *out) {
+  int model = 0, nchains = 0;
+  bool fp32 = false;
+  const ChainDesc *chains = nullptr;
+  CoefD cf{};
+  cudaStream_t st = nullptr;
+  if (!out || !state) return RK4_EINVAL;
+  if (handle_info(h, &model, &fp32, &nchains, &chains, &cf, &st) != RK4_OK) return RK4_EINVAL;
+  if (fp32 != (comp != nullptr)) return RK4_EINVAL;
+  if (nchains < 1 || nchains > kStaticMaxChains) return RK4_EINVAL;
+  StaticScratch *s = nullptr;
+  if (scratch_for_current_device(&s) != cudaSuccess) return RK4_ECUDA;
+  if (cudaMemsetAsync(&s->hdr, 0, sizeof(WsHeader), st) != cudaSuccess) return RK4_ECUDA;
+  if (nchains > 1 &&
+      cudaMemcpyAsync(s->chains, chains, sizeof(ChainDesc) * (size_t)nchains, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess)
+    return RK4_ECUDA;
+  if (launch_energy(model, fp32, state, comp, nchains, chains[0], s->chains, cf, s->partials, s->result, &s->hdr,
+                    st) != cudaSuccess)
+    return RK4_ECUDA;
+  int status = 0;
+  if (cudaMemcpyAsync(out, s->result, sizeof(double) * (size_t)nchains, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return RK4_ECUDA;
+  if (cudaMemcpyAsync(&status, &s->hdr.status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return RK4_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return RK4_ECUDA;
+  return (status & ST_NONFINITE) ? RK4_ENONFINITE : RK4_OK;
+}

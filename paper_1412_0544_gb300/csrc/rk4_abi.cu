@@ -428,6 +428,19 @@ rk4_chain *new_handle(int model, int precision, double dt, const rk4_params *p, 
 
 }  // namespace
 
+// Read-only view of a handle for the allocation-free reduction entry point.
+int rk4d::handle_info(const rk4_chain *h, int *model, bool *fp32, int *nchains, const ChainDesc **chains, CoefD *cf,
+                      cudaStream_t *stream) {
+  if (!h) return RK4_EINVAL;
+  *model = h->model;
+  *fp32 = h->fp32;
+  *nchains = h->nchains;
+  *chains = h->chains.data();
+  *cf = coef(h);
+  *stream = h->stream;
+  return RK4_OK;
+}
+
 extern "C" {
 
 void rk4_params_default(rk4_params *p) {

@@ -98,3 +98,11 @@ int blocked_max_threads(int model, bool fp32, int v);
 constexpr int kEnergyBlocks = 1024;  // fixed grid of the single-chain reduction (deterministic)
 
 }  // namespace rk4d
+
+struct rk4_chain;
+namespace rk4d {
+// Read-only view of a handle (model, precision, chain table on the host, coefficients, stream).
+int handle_info(const rk4_chain *h, int *model, bool *fp32, int *nchains, const ChainDesc **chains, CoefD *cf,
+                cudaStream_t *stream);
+
+}  // namespace rk4d
