@@ -27,10 +27,14 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+METRIC = "site-steps/s (RK4, fp64 & fp32-compensated) and % of GB300 HBM roofline"
+WORKLOAD = "roessler_chain_fp64_N2^24_1000steps"
 N_SITES = 1 << 24
 NSTEPS = 1000
 DT = 0.01
@@ -151,10 +155,11 @@ def run_reference(args):
     el = time.perf_counter() - t0
     value = sites * steps * args.steps / el
     sample = f"periodic Roessler chain N={sites}, {steps} RK4 steps per step, FP64, serial C oracle"
-    line = {"impl": "reference", "metric": "site-steps/s", "value": value, "unit": "site-steps/s",
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "site-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "roessler_chain_fp64_N2^24_1000steps", "sample": sample},
+            "config": {"workload": WORKLOAD, "sites": N_SITES, "rk4_steps_per_step": NSTEPS, "dt": DT,
+                       "boundary": "periodic", "sample": sample},
             "cpu_baseline": {"value": value, "unit": "site-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "site-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -173,8 +178,13 @@ def time_integrate(rk, h, st, cp, ws, nsteps, reps, torch):
     return e0.elapsed_time(e1) / 1e3
 
 
-def fp32_kahan_extra(rk, torch, stream, n=N_SITES, nsteps=NSTEPS, reps=2):
-    """FP32 state + Kahan-compensated update, same chain (configs: FP32 at N=2^24)."""
+def fp32_kahan_extra(rk, torch, stream, n=1 << 27, nsteps=NSTEPS):
+    """FP32 state + Kahan-compensated update on a periodic Roessler chain of N = 2^27 sites,
+    1000 steps; its half squared norm against the FP64 GPU path at the same size and steps,
+    and its error against the FP64 oracle on a separate 2^16-site chain from the same seed."""
+    import chain_inputs as ci
+    import oracle
+    out = {}
     h = rk.rk4_chain_create(rk.RK4_ROESSLER, rk.RK4_FP32_KAHAN, n, DT, rk.RK4_PERIODIC, None, stream)
     try:
         st = torch.empty((n, D), dtype=torch.float32, device="cuda")
@@ -182,15 +192,69 @@ def fp32_kahan_extra(rk, torch, stream, n=N_SITES, nsteps=NSTEPS, reps=2):
         cp = torch.zeros_like(st)
         ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
         best = rk.rk4_chain_autotune(h, st.clone(), cp.clone(), ws, 32)
-        rk.rk4_chain_integrate(h, st, cp, ws, 2 * best["k"])
-        el = time_integrate(rk, h, st, cp, ws, nsteps, reps, torch)
-        sps = n * nsteps * reps / el
+        rk.rk4_fill_uniform(st, n * D, SEED, 0, rk.RK4_FP32_KAHAN, stream)
+        cp.zero_()
+        e32_0 = rk.rk4_chain_energy(h, st, cp, ws)[0]
+        el = time_integrate(rk, h, st, cp, ws, nsteps, 1, torch)
+        e32 = rk.rk4_chain_energy(h, st, cp, ws)[0]
+        sps = n * nsteps / el
         launches = -(-nsteps // best["k"])
-        return {"value": sps, "unit": "site-steps/s", "N": n, "steps": nsteps, "tiling": best,
-                "effective_state_GBs": sps * 2 * D * 4 / 1e9,
-                "hbm_traffic_GBs_est": sps * 4 * D * 4 * (1 + 8 * best["k"] / best["G"]) / best["k"] / 1e9,
-                "fp32_pipe_frac_of_measured": sps * FP32K_INST_PER_SITE_STEP / FP32_INST_PEAK,
-                "ms_per_launch": 1e3 * el / (reps * launches)}
+        out.update({"value": sps, "unit": "site-steps/s", "N": n, "steps": nsteps, "tiling": best,
+                    "effective_state_GBs": sps * 2 * D * 4 / 1e9,
+                    "hbm_traffic_GBs_est": sps * 4 * D * 4 * (1 + 8 * best["k"] / best["G"]) / best["k"] / 1e9,
+                    "fp32_pipe_frac_of_measured": sps * FP32K_INST_PER_SITE_STEP / FP32_INST_PEAK,
+                    "ms_per_launch": 1e3 * el / launches, "half_norm2_t0": e32_0, "half_norm2_fp32": e32})
+        del st, cp, ws
+    finally:
+        rk.rk4_chain_destroy(h)
+    # the FP64 GPU path on the same chain, for the norm comparison
+    h = rk.rk4_chain_create(rk.RK4_ROESSLER, rk.RK4_FP64, n, DT, rk.RK4_PERIODIC, None, stream)
+    try:
+        s32 = torch.empty((n, D), dtype=torch.float32, device="cuda")
+        rk.rk4_fill_uniform(s32, n * D, SEED, 0, rk.RK4_FP32_KAHAN, stream)
+        st64 = s32.double()  # the FP32 start values, widened
+        del s32
+        ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+        rk.rk4_chain_set_tiling(h, 256, 4, 2)
+        rk.rk4_chain_integrate(h, st64, None, ws, nsteps)
+        e64 = rk.rk4_chain_energy(h, st64, None, ws)[0]
+        out["half_norm2_fp64_gpu"] = e64
+        out["half_norm2_rel_diff_vs_fp64_gpu"] = abs(out["half_norm2_fp32"] - e64) / abs(e64)
+        del st64, ws
+    finally:
+        rk.rk4_chain_destroy(h)
+    # error against the oracle on a separate 2^16-site chain (same seed, FP32 start values)
+    m = 1 << 16
+    y0 = ci.uniform_state(m, D, seed=SEED).astype(np.float32)
+    h = rk.rk4_chain_create(rk.RK4_ROESSLER, rk.RK4_FP32_KAHAN, m, DT, rk.RK4_PERIODIC, None, stream)
+    try:
+        st = torch.from_numpy(y0).cuda()
+        cp = torch.zeros_like(st)
+        ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+        rk.rk4_chain_set_tiling(h, best["block"], best["v"], best["k"])
+        rk.rk4_chain_integrate(h, st, cp, ws, nsteps)
+        got = (st.double() - cp.double()).cpu().numpy()
+    finally:
+        rk.rk4_chain_destroy(h)
+    ref = oracle.rk4_integrate(y0.astype(np.float64), oracle.ROESSLER, oracle.PERIODIC, DT, nsteps)
+    out["rel_err_vs_fp64_oracle_2e16"] = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+    return out
+
+
+def fixed_fp64_extra(rk, torch, stream, n=1 << 27, nsteps=200):
+    """Bandwidth-roofline configuration: FP64, fixed ends, N = 2^27 sites, 200 steps."""
+    h = rk.rk4_chain_create(rk.RK4_ROESSLER, rk.RK4_FP64, n, DT, rk.RK4_FIXED, None, stream)
+    try:
+        st = torch.empty((n, D), dtype=torch.float64, device="cuda")
+        rk.rk4_fill_uniform(st, n * D, SEED, 0, rk.RK4_FP64, stream)
+        ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+        rk.rk4_chain_set_tiling(h, 256, 4, 2)
+        rk.rk4_chain_integrate(h, st, None, ws, 4)
+        el = time_integrate(rk, h, st, None, ws, nsteps, 1, torch)
+        sps = n * nsteps / el
+        return {"value": sps, "unit": "site-steps/s", "N": n, "steps": nsteps, "boundary": "fixed",
+                "tiling": rk.rk4_chain_get_tiling(h), "effective_state_GBs": sps * 2 * D * 8 / 1e9,
+                "fp64_pipe_frac_of_measured": sps * FP64_INST_PER_SITE_STEP / FP64_INST_PEAK}
     finally:
         rk.rk4_chain_destroy(h)
 
@@ -232,7 +296,6 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
 
-    import numpy as np  # noqa: F401
     import torch
 
     from paper_1412_0544_gb300 import dist
@@ -313,19 +376,20 @@ def main():
 
     extras = {}
     if not args.no_extras:
-        extras["fp32_kahan"] = fp32_kahan_extra(rk, torch, stream)
-        extras["batch_fp64"] = batch_extra(rk, torch, stream, rk.RK4_FP64, nsteps=200)
-        extras["batch_fp32_kahan"] = batch_extra(rk, torch, stream, rk.RK4_FP32_KAHAN, nsteps=200)
+        extras["fixed_fp64_2e27"] = fixed_fp64_extra(rk, torch, stream)
+        extras["fp32_kahan_2e27"] = fp32_kahan_extra(rk, torch, stream)
+        extras["batch_fp64"] = batch_extra(rk, torch, stream, rk.RK4_FP64)
+        extras["batch_fp32_kahan"] = batch_extra(rk, torch, stream, rk.RK4_FP32_KAHAN)
     rk.rk4_chain_destroy(h)
 
     out = None
     if rank == 0:
         out = {
-            "metric": "site-steps/s (RK4, fp64 & fp32-compensated) and % of GB300 HBM roofline",
+            "metric": METRIC,
             "value": value, "unit": "site-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "roessler_chain_fp64_N2^24_1000steps", "sites": n, "rk4_steps_per_step": NSTEPS,
+            "config": {"workload": WORKLOAD, "sites": n, "rk4_steps_per_step": NSTEPS,
                        "dt": DT, "boundary": "periodic", "tiling": tiling, "l2": "inputs larger than L2 (403 MB state)",
                        "parallelism": f"replicas x{world}", "final_half_norm2": float(norm)},
             "roofline": roofline,
