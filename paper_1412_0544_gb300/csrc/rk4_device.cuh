@@ -62,8 +62,8 @@ __device__ __forceinline__ void slope(const R *u, R xl, R xr, const Coef<R> &cf,
 }
 
 // Stage j (0..3) bookkeeping after the slope k_j of a site is known: accumulate into acc and
-// form the next stage state u (Eq. (4)); stage 3 finishes the step (Eq. (5)) and leaves the
-// new state in both y and u.  cmp is the Kahan compensation (ignored unless KAHAN).
+// form the next stage state u (Eq. (4)); stage 3 finishes the step (Eq. (5)) in y (u is then
+// stale: the next step's stage 0 reads y).  cmp is the Kahan compensation (ignored unless KAHAN).
 template <typename R, int D, bool KAHAN>
 __device__ __forceinline__ void stage_update(int j, const R *k, R *y, R *u, R *acc, R *cmp, const Coef<R> &cf) {
 #pragma unroll
@@ -87,7 +87,6 @@ __device__ __forceinline__ void stage_update(int j, const R *k, R *y, R *u, R *a
       } else {
         y[d] = fma(cf.dt6, s4, y[d]);
       }
-      u[d] = y[d];
     }
   }
 }

@@ -24,7 +24,26 @@ constexpr unsigned kFull = 0xffffffffu;
 // (about 9 values per site plus temporaries) must fit 65536 registers per block.
 __host__ __device__ constexpr int max_threads_for(int v) { return v <= 1 ? 1024 : (v <= 4 ? 512 : 256); }
 
-// Advance the registers of one tile by K steps.  `edge` is 4 * 32 values of shared memory.
+// Store v to shared memory only when p holds, as a predicated instruction (no divergent
+// branch around it).
+__device__ __forceinline__ void st_shared_if(bool p, float *a, float v) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(a));
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.shared.f32 [%0], %1;\n\t}" ::"r"(s), "f"(v),
+               "r"(static_cast<int>(p))
+               : "memory");
+}
+__device__ __forceinline__ void st_shared_if(bool p, double *a, double v) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(a));
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.shared.f64 [%0], %1;\n\t}" ::"r"(s), "d"(v),
+               "r"(static_cast<int>(p))
+               : "memory");
+}
+
+// Advance the registers of one tile by K steps.  `edge` is 4 * 32 values of shared memory:
+// two alternating slots (by stage parity) of [first x of each warp | last x of each warp].
+// Stage 0 of every step reads y directly (it is the stage state), so no register copies are
+// needed between steps.  The warp-edge exchange is branch-free: predicated stores by lanes 0
+// and 31, uniform (broadcast) loads by every lane, and selects.
 template <typename R, int MODEL, int V, bool KAHAN, bool MASK>
 __device__ __forceinline__ void tile_advance(R (&y)[V][Dim<MODEL>::D], R (&cmp)[V][Dim<MODEL>::D],
                                              uint32_t ghost, int K, const Coef<R> &cf, R *edge) {
@@ -32,11 +51,10 @@ __device__ __forceinline__ void tile_advance(R (&y)[V][Dim<MODEL>::D], R (&cmp)[
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
+  const bool is_first = lane == 0, is_last = lane == 31;
+  const int prev = (warp > 0) ? warp - 1 : warp;      // tile ends read a stand-in (own warp)
+  const int next = (warp < nw - 1) ? warp + 1 : warp;
   R u[V][D], acc[V][D];
-#pragma unroll
-  for (int v = 0; v < V; ++v)
-#pragma unroll
-    for (int d = 0; d < D; ++d) u[v][d] = y[v][d];
 
 #pragma unroll 1
   for (int s = 0; s < K; ++s) {
@@ -44,21 +62,26 @@ __device__ __forceinline__ void tile_advance(R (&y)[V][Dim<MODEL>::D], R (&cmp)[
     for (int j = 0; j < 4; ++j) {
       R xs[V];
 #pragma unroll
-      for (int v = 0; v < V; ++v) xs[v] = (MASK && ((ghost >> v) & 1u)) ? R(0) : u[v][0];
+      for (int v = 0; v < V; ++v) {
+        const R x = (j == 0) ? y[v][0] : u[v][0];
+        xs[v] = (MASK && ((ghost >> v) & 1u)) ? R(0) : x;
+      }
       R left = __shfl_up_sync(kFull, xs[V - 1], 1);
       R right = __shfl_down_sync(kFull, xs[0], 1);
       R *eb = edge + (j & 1) * 64;  // [0,32): first x of each warp, [32,64): last x
-      if (lane == 0) eb[warp] = xs[0];
-      if (lane == 31) eb[32 + warp] = xs[V - 1];
+      st_shared_if(is_first, eb + warp, xs[0]);
+      st_shared_if(is_last, eb + 32 + warp, xs[V - 1]);
       __syncthreads();
-      if (lane == 0) left = (warp > 0) ? eb[32 + warp - 1] : xs[0];
-      if (lane == 31) right = (warp < nw - 1) ? eb[warp + 1] : xs[V - 1];
+      const R from_prev = eb[32 + prev];
+      const R from_next = eb[next];
+      left = is_first ? from_prev : left;
+      right = is_last ? from_next : right;
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         const R xl = (v == 0) ? left : xs[v - 1];
         const R xr = (v == V - 1) ? right : xs[v + 1];
         R k[D];
-        slope<R, MODEL>(u[v], xl, xr, cf, k);
+        slope<R, MODEL>((j == 0) ? y[v] : u[v], xl, xr, cf, k);
         stage_update<R, D, KAHAN>(j, k, y[v], u[v], acc[v], cmp[v], cf);
       }
     }
