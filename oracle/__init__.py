@@ -86,9 +86,10 @@ def _dp(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def params(a=0.2, b=1.0, c=9.0, kappa=1.0, omega0=1.0) -> np.ndarray:
-    """Parameter vector (a, b, c, kappa, omega0); defaults are Sec. 3.1's a=0.2, b=1, c=9."""
-    return np.array([a, b, c, kappa, omega0], dtype=np.float64)
+def params(a=0.2, b=1.0, c=9.0, kappa=1.0, omega0=1.0, kappa2=0.0) -> np.ndarray:
+    """Parameter vector (a, b, c, kappa, omega0, kappa2); defaults are Sec. 3.1's a=0.2, b=1,
+    c=9 with nearest-neighbour coupling only (kappa2 = 0)."""
+    return np.array([a, b, c, kappa, omega0, kappa2], dtype=np.float64)
 
 
 def _state(y0, model) -> np.ndarray:

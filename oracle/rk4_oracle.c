@@ -10,9 +10,12 @@
  * What it computes, by the paper's own definitions, with no blocking or fusion:
  *   - the homogeneous nearest-neighbour ODE of Eq. (2), r_i' = f(r_i) + g(r_i, r_{i-1}, r_{i+1});
  *   - f, g of the coupled Roessler chain, Eqs. (6)-(7), with a coupling strength kappa
- *     multiplying g (kappa = 1 is the paper's chain);
+ *     multiplying g (kappa = 1 is the paper's chain), optionally plus a next-nearest-neighbour
+ *     term kappa2 (x_{i-2} - 2 x_i + x_{i+2}) (the longer coupling range of Sec. 5; kappa2 = 0
+ *     is the paper's chain);
  *   - a harmonic (linear oscillator) chain from the same class (the oscillator chains of
- *     Sec. 2.1), with q' = p, p' = -omega0^2 q + kappa (q_{i-1} - 2 q_i + q_{i+1});
+ *     Sec. 2.1), with q' = p, p' = -omega0^2 q + kappa (q_{i-1} - 2 q_i + q_{i+1})
+ *     (+ kappa2 (q_{i-2} - 2 q_i + q_{i+2}));
  *   - periodic ends r_0 = r_N, r_{N+1} = r_1 (Sec. 3.1), or fixed ends r_0 = r_{N+1} = 0
  *     (not in the paper: a Dirichlet reading);
  *   - an explicit Runge-Kutta step in the paper's order, Eqs. (3)-(5): for each stage j the
@@ -40,9 +43,9 @@ enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2 };
 
 #define ORC_MAX_STAGES 16
 
-/* parameter vector layout shared with the Python wrapper: a, b, c, kappa, omega0 */
+/* parameter vector layout shared with the Python wrapper: a, b, c, kappa, omega0, kappa2 */
 typedef struct {
-  double a, b, c, kappa, omega0;
+  double a, b, c, kappa, omega0, kappa2;
 } orc_params;
 
 int oracle_dim(int model) {
@@ -65,25 +68,41 @@ static void neighbours(int bc, int64_t n, int D, const double *r, int64_t i, dou
   }
 }
 
+/* Coupling coordinate of the second neighbours i-2 and i+2 (zero beyond fixed ends). */
+static void neighbours2(int bc, int64_t n, int D, const double *r, int64_t i, double *xl, double *xr) {
+  if (bc == ORC_PERIODIC) {
+    int64_t il = ((i - 2) % n + n) % n;
+    int64_t ir = (i + 2) % n;
+    *xl = r[il * D];
+    *xr = r[ir * D];
+  } else {
+    *xl = (i - 2 < 0) ? 0.0 : r[(i - 2) * D];
+    *xr = (i + 2 > n - 1) ? 0.0 : r[(i + 2) * D];
+  }
+}
+
 /* Eq. (3): k_i = f(r_i) + g(r_i, r_{i-1}, r_{i+1}) for every site, one sweep. */
 static void rhs(int model, int bc, int64_t n, const orc_params *p, const double *r, double *k) {
   const int D = oracle_dim(model);
   for (int64_t i = 0; i < n; ++i) {
-    double xl, xr;
+    double xl, xr, xl2, xr2;
     neighbours(bc, n, D, r, i, &xl, &xr);
+    neighbours2(bc, n, D, r, i, &xl2, &xr2);
     const double *ri = r + i * D;
     double *ki = k + i * D;
     if (model == ORC_ROESSLER) {
       double x = ri[0], y = ri[1], z = ri[2];
-      double lap = xl - 2.0 * x + xr; /* Eq. (7), first component */
-      ki[0] = -y - z + p->kappa * lap; /* Eq. (6) f_x plus coupling */
-      ki[1] = x + p->a * y;            /* Eq. (6) f_y */
-      ki[2] = p->b + z * (x - p->c);   /* Eq. (6) f_z */
+      double lap = xl - 2.0 * x + xr;   /* Eq. (7), first component */
+      double lap2 = xl2 - 2.0 * x + xr2; /* second neighbours */
+      ki[0] = -y - z + p->kappa * lap + p->kappa2 * lap2; /* Eq. (6) f_x plus coupling */
+      ki[1] = x + p->a * y;                               /* Eq. (6) f_y */
+      ki[2] = p->b + z * (x - p->c);                      /* Eq. (6) f_z */
     } else {
       double q = ri[0], pm = ri[1];
       double lap = xl - 2.0 * q + xr;
+      double lap2 = xl2 - 2.0 * q + xr2;
       ki[0] = pm;
-      ki[1] = -p->omega0 * p->omega0 * q + p->kappa * lap;
+      ki[1] = -p->omega0 * p->omega0 * q + p->kappa * lap + p->kappa2 * lap2;
     }
   }
 }
@@ -96,7 +115,7 @@ int oracle_rk_integrate(int model, int bc, int64_t n, const double *prm, int s, 
   const int D = oracle_dim(model);
   if (D == 0 || n < 1 || s < 1 || s > ORC_MAX_STAGES || (bc != ORC_PERIODIC && bc != ORC_FIXED))
     return ORC_EINVAL;
-  orc_params p = {prm[0], prm[1], prm[2], prm[3], prm[4]};
+  orc_params p = {prm[0], prm[1], prm[2], prm[3], prm[4], prm[5]};
   const int64_t len = n * D;
   double *k = (double *)malloc(sizeof(double) * (size_t)len * (size_t)s);
   double *r = (double *)malloc(sizeof(double) * (size_t)len);
@@ -141,17 +160,23 @@ int oracle_rk4_integrate(int model, int bc, int64_t n, const double *prm, double
 /* The slope field F(r) alone (one Eq. (3) sweep), exposed for tests. */
 int oracle_rhs(int model, int bc, int64_t n, const double *prm, const double *r, double *k) {
   if (oracle_dim(model) == 0 || n < 1) return ORC_EINVAL;
-  orc_params p = {prm[0], prm[1], prm[2], prm[3], prm[4]};
+  orc_params p = {prm[0], prm[1], prm[2], prm[3], prm[4], prm[5]};
   rhs(model, bc, n, &p, r, k);
   return ORC_OK;
 }
 
-/* Harmonic-chain energy H = sum_i (p_i^2/2 + omega0^2 q_i^2/2) + kappa/2 sum_bonds (dq)^2.
- * Periodic: N bonds (q_{N+1} = q_1).  Fixed: N+1 bonds including the two to the zero
- * ghosts q_0 = q_{N+1} = 0.  H is the Hamiltonian whose equations of motion are the
- * harmonic chain above. */
+/* Harmonic-chain energy H = sum_i (p_i^2/2 + omega0^2 q_i^2/2) + kappa/2 sum_bonds (dq)^2
+ * + kappa2/2 sum_second-bonds (q_{i+2} - q_i)^2.  Periodic: N bonds of each kind (indices mod
+ * N).  Fixed: every bond with at least one end in the chain, the other end possibly a zero
+ * ghost (N+1 nearest bonds, N+2 second-neighbour bonds).  H is the Hamiltonian whose
+ * equations of motion are the harmonic chain above. */
+static double q_at(int bc, int64_t n, const double *y, int64_t i) {
+  if (bc == ORC_PERIODIC) return y[2 * (((i % n) + n) % n)];
+  return (i < 0 || i >= n) ? 0.0 : y[2 * i];
+}
+
 double oracle_energy_harmonic(int bc, int64_t n, const double *prm, const double *y) {
-  const double kappa = prm[3], w2 = prm[4] * prm[4];
+  const double kappa = prm[3], w2 = prm[4] * prm[4], kappa2 = prm[5];
   double e = 0.0;
   for (int64_t i = 0; i < n; ++i) {
     double q = y[2 * i], pm = y[2 * i + 1];
@@ -168,6 +193,13 @@ double oracle_energy_harmonic(int bc, int64_t n, const double *prm, const double
       double qr = (i + 1 >= n) ? 0.0 : y[2 * (i + 1)];
       double d = qr - ql;
       e += 0.5 * kappa * d * d;
+    }
+  }
+  if (kappa2 != 0.0) {
+    const int64_t first = (bc == ORC_PERIODIC) ? 0 : -2;
+    for (int64_t i = first; i < n; ++i) {
+      double d = q_at(bc, n, y, i + 2) - q_at(bc, n, y, i);
+      e += 0.5 * kappa2 * d * d;
     }
   }
   return e;

@@ -21,11 +21,16 @@ import numpy as np
 import scipy.fft as sfft
 
 
-def mode_frequencies(n: int, bc: int, kappa: float, omega0: float) -> np.ndarray:
-    """omega_m for the modes in the order the transform below produces them."""
+def mode_frequencies(n: int, bc: int, kappa: float, omega0: float, kappa2: float = 0.0) -> np.ndarray:
+    """omega_m for the modes in the order the transform below produces them.  Second-neighbour
+    coupling kappa2 keeps the Fourier modes (periodic ends only): it adds
+    4 kappa2 sin^2(2 pi m / N)."""
     if bc == 0:
         m = np.arange(n)
-        return np.sqrt(omega0 ** 2 + 4.0 * kappa * np.sin(np.pi * m / n) ** 2)
+        return np.sqrt(omega0 ** 2 + 4.0 * kappa * np.sin(np.pi * m / n) ** 2
+                       + 4.0 * kappa2 * np.sin(2.0 * np.pi * m / n) ** 2)
+    if kappa2 != 0.0:
+        raise ValueError("second-neighbour coupling with fixed ends has no sine-mode closed form")
     m = np.arange(1, n + 1)
     return np.sqrt(omega0 ** 2 + 4.0 * kappa * np.sin(np.pi * m / (2.0 * (n + 1))) ** 2)
 
@@ -38,11 +43,12 @@ def _inverse(v, bc: int) -> np.ndarray:
     return np.real(sfft.ifft(v)) if bc == 0 else sfft.idst(v, type=1)
 
 
-def _evolve(y0: np.ndarray, bc: int, kappa: float, omega0: float, amp: np.ndarray, ang: np.ndarray) -> np.ndarray:
+def _evolve(y0: np.ndarray, bc: int, kappa: float, omega0: float, amp: np.ndarray, ang: np.ndarray,
+            kappa2: float = 0.0) -> np.ndarray:
     """Apply amp * Rot(ang) in scaled mode coordinates (q, p / w) to every mode."""
     y0 = np.asarray(y0, dtype=np.float64).reshape(-1, 2)
     n = y0.shape[0]
-    w = mode_frequencies(n, bc, kappa, omega0)
+    w = mode_frequencies(n, bc, kappa, omega0, kappa2)
     qh = _forward(y0[:, 0], bc)
     sh = _forward(y0[:, 1], bc) / w
     c, s = np.cos(ang), np.sin(ang)
@@ -54,16 +60,16 @@ def _evolve(y0: np.ndarray, bc: int, kappa: float, omega0: float, amp: np.ndarra
     return out
 
 
-def rk4_modal(y0, bc: int, kappa: float, omega0: float, dt: float, nsteps: int) -> np.ndarray:
+def rk4_modal(y0, bc: int, kappa: float, omega0: float, dt: float, nsteps: int, kappa2: float = 0.0) -> np.ndarray:
     """Exact (up to rounding) result of nsteps classical RK4 steps on the harmonic chain."""
     n = np.asarray(y0).reshape(-1, 2).shape[0]
-    w = mode_frequencies(n, bc, kappa, omega0)
+    w = mode_frequencies(n, bc, kappa, omega0, kappa2)
     h = w * dt
     alpha = 1.0 - h ** 2 / 2.0 + h ** 4 / 24.0
     beta = 1.0 - h ** 2 / 6.0
     rho = alpha ** 2 + (beta * h) ** 2
     theta = np.arctan2(beta * h, alpha)
-    return _evolve(y0, bc, kappa, omega0, rho ** (nsteps / 2.0), nsteps * theta)
+    return _evolve(y0, bc, kappa, omega0, rho ** (nsteps / 2.0), nsteps * theta, kappa2)
 
 
 def exact_flow(y0, bc: int, kappa: float, omega0: float, t: float) -> np.ndarray:
@@ -73,11 +79,11 @@ def exact_flow(y0, bc: int, kappa: float, omega0: float, t: float) -> np.ndarray
     return _evolve(y0, bc, kappa, omega0, np.ones_like(w), w * t)
 
 
-def modal_energy(y0, bc: int, kappa: float, omega0: float) -> np.ndarray:
+def modal_energy(y0, bc: int, kappa: float, omega0: float, kappa2: float = 0.0) -> np.ndarray:
     """Per-mode energies (1/2)(|p_m|^2 + w_m^2 |q_m|^2), normalised so they sum to H."""
     y0 = np.asarray(y0, dtype=np.float64).reshape(-1, 2)
     n = y0.shape[0]
-    w = mode_frequencies(n, bc, kappa, omega0)
+    w = mode_frequencies(n, bc, kappa, omega0, kappa2)
     qh = _forward(y0[:, 0], bc)
     ph = _forward(y0[:, 1], bc)
     # Parseval factors: sum |v|^2 = (1/N) sum |fft v|^2;  for DST-I: sum |v|^2 = sum |dst v|^2 / (2 (N+1))

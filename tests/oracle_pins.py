@@ -84,31 +84,39 @@ def pin_roessler_fixed_point(lib, n=16, nsteps=1000, dt=0.01, tol=1e-12):
     return worst < tol, f"Roessler equilibria drift {worst:.2e}"
 
 
-def roessler_chain_rhs(bc, kappa, a=0.2, b=1.0, c=9.0):
-    """Eq. (2) with f, g of Eqs. (6)-(7) as whole-array numpy (for scipy's integrator)."""
+def roessler_chain_rhs(bc, kappa, a=0.2, b=1.0, c=9.0, kappa2=0.0):
+    """Eq. (2) with f, g of Eqs. (6)-(7) as whole-array numpy (for scipy's integrator), plus an
+    optional second-neighbour coupling kappa2."""
+    def shifted(x, s):  # x_{i+s}, zero beyond fixed ends
+        if bc == PER:
+            return np.roll(x, -s)
+        out = np.zeros_like(x)
+        if s > 0:
+            out[:-s] = x[s:]
+        else:
+            out[-s:] = x[:s]
+        return out
+
     def F(_t, v):
         r = v.reshape(-1, 3)
         x, y, z = r[:, 0], r[:, 1], r[:, 2]
-        if bc == PER:
-            xl, xr = np.roll(x, 1), np.roll(x, -1)
-        else:
-            xl = np.concatenate(([0.0], x[:-1]))
-            xr = np.concatenate((x[1:], [0.0]))
+        xl, xr = shifted(x, -1), shifted(x, 1)
+        xl2, xr2 = shifted(x, -2), shifted(x, 2)
         out = np.empty_like(r)
-        out[:, 0] = -y - z + kappa * (xl - 2 * x + xr)
+        out[:, 0] = -y - z + kappa * (xl - 2 * x + xr) + kappa2 * (xl2 - 2 * x + xr2)
         out[:, 1] = x + a * y
         out[:, 2] = b + z * (x - c)
         return out.reshape(-1)
     return F
 
 
-def pin_roessler_vs_dop853(lib, n=6, bc=PER, kappa=1.0, T=0.5):
+def pin_roessler_vs_dop853(lib, n=6, bc=PER, kappa=1.0, T=0.5, kappa2=0.0):
     """RK4 converges at fourth order to scipy's DOP853 solution of the paper's equations."""
     y0 = ci.uniform_state(n, 3, seed=4000 + n + bc)
-    sol = solve_ivp(roessler_chain_rhs(bc, kappa), (0.0, T), y0.reshape(-1), method="DOP853",
+    sol = solve_ivp(roessler_chain_rhs(bc, kappa, kappa2=kappa2), (0.0, T), y0.reshape(-1), method="DOP853",
                     rtol=1e-13, atol=1e-13)
     ref = sol.y[:, -1].reshape(-1, 3)
-    prm = oracle.params(kappa=kappa)
+    prm = oracle.params(kappa=kappa, kappa2=kappa2)
     errs = []
     for dt in (0.025, 0.0125, 0.00625):
         got = oracle.rk4_integrate(y0, ROE, bc, dt, int(round(T / dt)), prm, lib=lib)
@@ -149,26 +157,28 @@ def brute_force_rk4(y0, model, bc, prm, dt, nsteps, dps=40):
     """Classical RK4 as a dense vector map in mpmath, neighbours from explicit lists."""
     import mpmath as mp
     mp.mp.dps = dps
-    a, b, c, kappa, omega0 = (mp.mpf(float(v)) for v in prm)
+    a, b, c, kappa, omega0, kappa2 = (mp.mpf(float(v)) for v in prm)
     y = [[mp.mpf(float(v)) for v in row] for row in np.asarray(y0)]
     n = len(y)
-    if bc == PER:
-        nb = [((i - 1) % n, (i + 1) % n) for i in range(n)]
-    else:
-        nb = [(i - 1 if i > 0 else None, i + 1 if i < n - 1 else None) for i in range(n)]
+
+    def at(i):  # explicit neighbour lists: an index, or None for a fixed-end ghost
+        if bc == PER:
+            return i % n
+        return i if 0 <= i < n else None
+
+    nb = [(at(i - 1), at(i + 1), at(i - 2), at(i + 2)) for i in range(n)]
     h = mp.mpf(float(dt))
 
     def F(state):
         out = []
-        for i, (l, r) in enumerate(nb):
-            xl = state[l][0] if l is not None else mp.mpf(0)
-            xr = state[r][0] if r is not None else mp.mpf(0)
+        for i, idx in enumerate(nb):
+            xl, xr, xl2, xr2 = (state[j][0] if j is not None else mp.mpf(0) for j in idx)
             s = state[i]
-            lap = xl + xr - 2 * s[0]
+            g = kappa * (xl + xr - 2 * s[0]) + kappa2 * (xl2 + xr2 - 2 * s[0])
             if model == ROE:
-                out.append([-s[1] - s[2] + kappa * lap, s[0] + a * s[1], b + s[2] * (s[0] - c)])
+                out.append([-s[1] - s[2] + g, s[0] + a * s[1], b + s[2] * (s[0] - c)])
             else:
-                out.append([s[1], -omega0 ** 2 * s[0] + kappa * lap])
+                out.append([s[1], -omega0 ** 2 * s[0] + g])
         return out
 
     def axpy(u, alpha, v):
@@ -184,10 +194,10 @@ def brute_force_rk4(y0, model, bc, prm, dt, nsteps, dps=40):
     return np.array([[float(v) for v in row] for row in y])
 
 
-def pin_brute_force(lib, n=4, model=ROE, bc=PER, nsteps=100, dt=0.01, tol=1e-13):
+def pin_brute_force(lib, n=4, model=ROE, bc=PER, nsteps=100, dt=0.01, tol=1e-13, kappa2=0.0):
     D = oracle.dim(model)
     y0 = ci.uniform_state(n, D, seed=7000 + n + 10 * model + bc)
-    prm = oracle.params(kappa=1.25, omega0=0.8)
+    prm = oracle.params(kappa=1.25, omega0=0.8, kappa2=kappa2)
     got = oracle.rk4_integrate(y0, model, bc, dt, nsteps, prm, lib=lib)
     ref = brute_force_rk4(y0, model, bc, prm, dt, nsteps)
     err = cf.rel_inf(got, ref)
@@ -269,6 +279,55 @@ def pin_tableau_orders(lib, n=16, T=1.0):
     return ok, f"observed orders {detail}"
 
 
+# ---- next-nearest-neighbour coupling (the longer coupling range of Sec. 5) --------------
+
+def pin_nnn_modal(lib, n=48, nsteps=800, dt=0.01, kappa=1.1, kappa2=0.6, omega0=0.8, tol=1e-12):
+    """Periodic harmonic chain with second-neighbour coupling: Fourier modes still diagonalise
+    it, omega_m^2 = omega0^2 + 4 kappa sin^2(pi m/N) + 4 kappa2 sin^2(2 pi m/N)."""
+    y0 = ci.uniform_state(n, 2, seed=9100 + n)
+    prm = oracle.params(kappa=kappa, omega0=omega0, kappa2=kappa2)
+    got = oracle.rk4_integrate(y0, HAR, PER, dt, nsteps, prm, lib=lib)
+    ref = cf.rk4_modal(y0, PER, kappa, omega0, dt, nsteps, kappa2=kappa2)
+    e0 = oracle.energy_harmonic(y0, PER, prm, lib=lib)
+    e0_ref = float(np.sum(cf.modal_energy(y0, PER, kappa, omega0, kappa2=kappa2)))
+    err = cf.rel_inf(got, ref)
+    ok = err < tol and abs(e0 - e0_ref) < tol * e0_ref
+    return ok, f"NNN harmonic modal: rel err {err:.2e}, energy rel {abs(e0 - e0_ref) / e0_ref:.2e}"
+
+
+def pin_nnn_energy_fixed(lib, n=12, nsteps=400, dt=0.02):
+    """Fixed ends with second-neighbour bonds: the energy (ghost bonds included) is conserved
+    by the exact flow, so RK4's drift is O(dt^4) per unit time and shrinks ~2^4 per halving."""
+    y0 = ci.uniform_state(n, 2, seed=9200)
+    prm = oracle.params(kappa=1.0, omega0=1.0, kappa2=0.7)
+    e0 = oracle.energy_harmonic(y0, FIX, prm, lib=lib)
+    drifts = []
+    for k in range(3):
+        h = dt / 2 ** k
+        y = oracle.rk4_integrate(y0, HAR, FIX, h, nsteps * 2 ** k, prm, lib=lib)
+        drifts.append(abs(oracle.energy_harmonic(y, FIX, prm, lib=lib) - e0) / e0)
+    orders = [float(np.log2(drifts[i] / drifts[i + 1])) for i in range(2)]
+    ok = all(3.5 < p < 6.5 for p in orders)
+    return ok, f"NNN fixed-end energy drift {drifts}, orders {orders}"
+
+
+def pin_nnn_cone(lib, n=96, site=48):
+    """With second neighbours the influence of one site spreads exactly 2 sites per stage, 8 per
+    step (twice the overlap, as Sec. 5 says for next-nearest coupling)."""
+    y0 = ci.uniform_state(n, 3, seed=9300)
+    y1 = y0.copy()
+    y1[site, 0] += 0.5
+    prm = oracle.params(kappa=5.0, kappa2=10.0)
+    detail, ok = [], True
+    for m in (1, 2):
+        a = oracle.rk4_integrate(y0, ROE, FIX, 0.1, m, prm, lib=lib)
+        b = oracle.rk4_integrate(y1, ROE, FIX, 0.1, m, prm, lib=lib)
+        changed = np.nonzero(np.any(a != b, axis=1))[0]
+        detail.append((m, int(changed.min()), int(changed.max())))
+        ok &= changed.min() == site - 8 * m and changed.max() == site + 8 * m
+    return ok, f"NNN cone {detail}"
+
+
 ALL_PINS = [
     ("harmonic_modal_per", lambda lib: pin_harmonic_modal(lib, bc=PER)),
     ("harmonic_modal_fix", lambda lib: pin_harmonic_modal(lib, bc=FIX)),
@@ -288,4 +347,10 @@ ALL_PINS = [
     ("reflection", pin_reflection),
     ("cone", pin_dependency_cone),
     ("tableau_orders", pin_tableau_orders),
+    ("nnn_modal", pin_nnn_modal),
+    ("nnn_energy_fixed", pin_nnn_energy_fixed),
+    ("nnn_cone", pin_nnn_cone),
+    ("nnn_dop853_fix", lambda lib: pin_roessler_vs_dop853(lib, bc=FIX, kappa=1.2, kappa2=0.7)),
+    ("nnn_brute_per", lambda lib: pin_brute_force(lib, n=5, model=ROE, bc=PER, kappa2=0.9)),
+    ("nnn_brute_fix", lambda lib: pin_brute_force(lib, n=6, model=HAR, bc=FIX, kappa2=0.9)),
 ]

@@ -63,12 +63,19 @@ def test_batch_equals_separate_chains(lib):
 
 # (label, original text, planted mistake) -- each original must occur exactly once
 MUTANTS = [
-    ("drop coupling", "ki[0] = -y - z + p->kappa * lap;", "ki[0] = -y - z;"),
+    ("drop coupling", "ki[0] = -y - z + p->kappa * lap + p->kappa2 * lap2;", "ki[0] = -y - z + p->kappa2 * lap2;"),
+    ("drop second-neighbour coupling", "ki[0] = -y - z + p->kappa * lap + p->kappa2 * lap2;",
+     "ki[0] = -y - z + p->kappa * lap;"),
+    ("second-neighbour index", "int64_t ir = (i + 2) % n;", "int64_t ir = (i + 1) % n;"),
+    ("second-neighbour fixed ghost", "*xl = (i - 2 < 0) ? 0.0 : r[(i - 2) * D];", "*xl = (i - 2 < 0) ? r[0] : r[(i - 2) * D];"),
+    ("harmonic second-neighbour sign", "q + p->kappa * lap + p->kappa2 * lap2;", "q + p->kappa * lap - p->kappa2 * lap2;"),
+    ("energy second-neighbour ghost bonds", "const int64_t first = (bc == ORC_PERIODIC) ? 0 : -2;",
+     "const int64_t first = 0;"),
     ("sign f_y", "ki[1] = x + p->a * y;", "ki[1] = x - p->a * y;"),
     ("transposed f_z", "ki[2] = p->b + z * (x - p->c);", "ki[2] = p->b + x * (z - p->c);"),
     ("laplacian index", "double lap = xl - 2.0 * x + xr;", "double lap = xl - 2.0 * x + xl;"),
     ("harmonic omega not squared", "ki[1] = -p->omega0 * p->omega0 * q", "ki[1] = -p->omega0 * q"),
-    ("harmonic coupling sign", "q + p->kappa * lap;", "q - p->kappa * lap;"),
+    ("harmonic coupling sign", "q + p->kappa * lap + p->kappa2 * lap2;", "q - p->kappa * lap + p->kappa2 * lap2;"),
     ("periodic wrap", "int64_t il = (i == 0) ? n - 1 : i - 1;", "int64_t il = (i == 0) ? 0 : i - 1;"),
     ("free end instead of fixed", "*xl = (i == 0) ? 0.0 : r[(i - 1) * D];", "*xl = (i == 0) ? r[0] : r[(i - 1) * D];"),
     ("weights b", "{1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0}", "{1.0 / 6.0, 1.0 / 6.0, 1.0 / 2.0, 1.0 / 6.0}"),
