@@ -281,6 +281,57 @@ def batch_extra(rk, torch, stream, precision, nsteps=NSTEPS):
         rk.rk4_chain_destroy(h)
 
 
+def size_sweep(args):
+    """Site-steps/s against chain length N = 2^10 .. 2^27 (the GPU counterpart of the paper's
+    size-dependence study, Sec. 3.2.3): the standard scheme (one launch per stage, Sec. 2.2)
+    against temporal blocking and the persistent kernel, FP64 and FP32-Kahan, periodic
+    Roessler chain.  Prints one JSON object per (N, precision, scheme)."""
+    import torch
+    import paper_1412_0544_gb300 as rk
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    schemes = [("standard", rk.RK4_KERNEL_STAGED), ("blocked", rk.RK4_KERNEL_BLOCKED),
+               ("persistent", rk.RK4_KERNEL_PERSISTENT)]
+    lo, hi = args.sweep_min, args.sweep_max
+    tuned = {}  # the paper finds the optimal cluster size independent of N: tune up to 2^22, then reuse
+    for p in range(lo, hi + 1):
+        n = 1 << p
+        for prec, pname in ((rk.RK4_FP64, "fp64"), (rk.RK4_FP32_KAHAN, "fp32_kahan")):
+            dtype = torch.float64 if prec == rk.RK4_FP64 else torch.float32
+            st0 = torch.empty((n, D), dtype=dtype, device="cuda")
+            rk.rk4_fill_uniform(st0, n * D, SEED, 0, prec, stream)
+            for sname, kern in schemes:
+                h = rk.rk4_chain_create(rk.RK4_ROESSLER, prec, n, DT, rk.RK4_PERIODIC, None, stream)
+                try:
+                    rk.rk4_chain_set_kernel(h, kern)
+                    st = st0.clone()
+                    cp = torch.zeros_like(st) if prec == rk.RK4_FP32_KAHAN else None
+                    ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+                    tiling = None
+                    if kern != rk.RK4_KERNEL_STAGED:
+                        if p <= 22 or (pname, sname) not in tuned:
+                            tiling = rk.rk4_chain_autotune(h, st.clone(), cp.clone() if cp is not None else None,
+                                                           ws, 32)
+                            tuned[(pname, sname)] = tiling
+                        else:
+                            tiling = tuned[(pname, sname)]
+                            rk.rk4_chain_set_tiling(h, tiling["block"], tiling["v"], tiling["k"])
+                    # about 2^31 site-steps per measurement (at least 32 steps)
+                    nsteps = max(32, min(4096, (1 << 31) // n))
+                    if kern == rk.RK4_KERNEL_STAGED:
+                        nsteps = max(8, nsteps // 4)
+                    rk.rk4_chain_integrate(h, st, cp, ws, nsteps)  # warm-up, graph capture
+                    el = min(time_integrate(rk, h, st, cp, ws, nsteps, 1, torch) for _ in range(3))
+                    print(json.dumps({"N": n, "precision": pname, "scheme": sname, "site_steps_per_s": n * nsteps / el,
+                                      "steps": nsteps, "tiling": tiling,
+                                      "state_MB": n * D * (8 if prec == rk.RK4_FP64 else 4) / 1e6}), flush=True)
+                    del st, cp, ws
+                finally:
+                    rk.rk4_chain_destroy(h)
+            del st0
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -290,11 +341,16 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the FP32 and batch side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tiling", default=None, help="block,v,k of the FP64 kernel instead of the autotuner's pick")
+    ap.add_argument("--sweep", action="store_true", help="site-steps/s against chain length instead of the bench line")
+    ap.add_argument("--sweep-min", type=int, default=10, help="log2 of the smallest N of --sweep")
+    ap.add_argument("--sweep-max", type=int, default=27, help="log2 of the largest N of --sweep")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return size_sweep(args)
 
     import torch
 
