@@ -82,11 +82,12 @@ typedef struct {
   double omega0;   /* harmonic chain on-site frequency */
 } rk4_params;
 
-/* Tiling of the blocked kernels: a tile is block * v sites, of which G = block * v - 8 k are
- * written back (the rest is the 4k-site halo on each side). */
+/* Tiling of the blocked kernels: a tile is block * v sites, of which G = block * v - 2 H are
+ * written back, H = 4k (classical RK4) or s * range * k (generic scheme) being the halo on each
+ * side. */
 typedef struct {
   int block;  /* threads per block: 64 .. 1024, a multiple of 32 */
-  int v;      /* consecutive sites per thread: 1, 2, 4 or 8 */
+  int v;      /* consecutive sites per thread: 1, 2, 4 or 8 (generic kernels: 2 or 4) */
   int k;      /* RK4 steps per launch: 1 .. 16 */
   int G;      /* output: interior sites per tile */
 } rk4_tiling;
@@ -125,6 +126,23 @@ int rk4_chain_set_kernel(rk4_chain *h, int kernel);
  * Errors: RK4_EINVAL when block, v or k is out of range or G < 8k. */
 int rk4_chain_set_tiling(rk4_chain *h, int block, int v, int k);
 int rk4_chain_get_tiling(const rk4_chain *h, rk4_tiling *out);
+
+/* Replaces the classical RK4 tableau with any explicit Runge-Kutta tableau of 1 <= s <= 7
+ * stages (the paper notes the technique applies to any explicit RK method, Sec. 2): A is s x s
+ * row-major and must be strictly lower triangular, b holds the s weights (Eqs. (4)-(5)); both
+ * are copied.  s = 0 restores the classical RK4 kernels.  The generic kernels keep every stage
+ * slope per site and need a halo of s * range sites per side per step; tilings then use v = 2
+ * or 4 sites per thread.  The persistent kernel does not support them (RK4_EUNSUPPORTED).
+ * Resets the tiling to its default.  Errors: RK4_EINVAL. */
+int rk4_chain_set_tableau(rk4_chain *h, int s, const double *A, const double *b);
+
+/* Second-neighbour coupling strength kappa2: the coupling becomes
+ * kappa (x_{i-1} - 2 x_i + x_{i+1}) + kappa2 (x_{i-2} - 2 x_i + x_{i+2}) (the longer coupling
+ * range of Sec. 5, which needs twice the overlap).  kappa2 != 0 selects the generic kernels
+ * (with the current tableau, classical RK4 by default); the harmonic energy then includes the
+ * second-neighbour bonds.  0 restores nearest-neighbour coupling.  Resets the tiling to its
+ * default.  Errors: RK4_EINVAL. */
+int rk4_chain_set_coupling2(rk4_chain *h, double kappa2);
 
 /* Times the candidate tilings on the caller's buffers and keeps the fastest (the paper
  * picks G by a performance study, Sec. 3.2.1).  The call integrates `state` (and comp)

@@ -70,6 +70,8 @@ def _load():
         "rk4_chain_set_option": (c_int, [H, c_int, i64]),
         "rk4_debug_barrier_timeout": (c_int, [H, vp, vp, vp, sz, i64]),
         "rk4_chain_set_time": (c_int, [H, ctypes.c_double]),
+        "rk4_chain_set_tableau": (c_int, [H, c_int, dp, dp]),
+        "rk4_chain_set_coupling2": (c_int, [H, ctypes.c_double]),
         "rk4_chain_destroy": (c_int, [H]),
         "rk4_strerror": (ctypes.c_char_p, [c_int]),
         "rk4_fill_uniform": (c_int, [vp, i64, ctypes.c_uint64, ctypes.c_uint64, c_int, vp]),
@@ -271,6 +273,24 @@ def rk4_debug_barrier_timeout(h, state, comp, ws, timeout_ns: int, ws_bytes: int
     wb = _nbytes(ws) if ws_bytes is None else ws_bytes
     _check(_lib.rk4_debug_barrier_timeout(h, _ptr(state), _ptr(comp), _ptr(ws), wb, int(timeout_ns)),
            "rk4_debug_barrier_timeout")
+
+
+def rk4_chain_set_tableau(h, A=None, b=None):
+    """Any explicit tableau (A strictly lower s x s, weights b, s <= 7); None restores RK4."""
+    if A is None:
+        _check(_lib.rk4_chain_set_tableau(h, 0, None, None), "rk4_chain_set_tableau")
+        return
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    s = b.shape[0]
+    if A.shape != (s, s):
+        raise ValueError("tableau shape mismatch")
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(_lib.rk4_chain_set_tableau(h, s, A.ctypes.data_as(dp), b.ctypes.data_as(dp)), "rk4_chain_set_tableau")
+
+
+def rk4_chain_set_coupling2(h, kappa2: float):
+    _check(_lib.rk4_chain_set_coupling2(h, float(kappa2)), "rk4_chain_set_coupling2")
 
 
 def rk4_chain_set_time(h, t0: float):

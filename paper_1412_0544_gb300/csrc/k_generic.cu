@@ -1,0 +1,371 @@
+// k_generic.cu -- any explicit Runge-Kutta tableau (up to 7 stages) and coupling range 1 or 2
+// (nearest or next-nearest neighbours), the generalisations the paper names in Sec. 2 ("any
+// other explicit Runge-Kutta method") and Sec. 5 ("next-nearest-neighbour couplings need twice
+// as long overlaps").  Temporal blocking then needs a halo of s * range sites per side per
+// step (s stages, each reaching `range` sites further).
+//
+// Two schemes share one per-site operation sequence (so they agree bit for bit):
+//   * k_gen_state / k_gen_slope / k_gen_combine: the standard implementation, one sweep per
+//     stage-state evaluation, one per slope evaluation and one for the combination (2s+1 sweeps
+//     per step, Sec. 2.2);
+//   * k_gen_blocked: tiles of W = block * v sites advanced k steps per launch in registers.
+//
+// Per-site operation order (fixed):
+//   stage state  u = y; for m < j with a_jm != 0:  u = fma(a_jm dt, k_m, u)        (Eq. (4))
+//   slope        range 1: as the RK4 kernels; range 2 adds lap2 = fma(-2, x, x_{i-2} + x_{i+2})
+//                inside the coupling: kx = fma(kappa, lap, fma(kappa2, lap2, -(y + z)))
+//   combine      inc = 0; for m with b_m != 0: inc = fma(b_m dt, k_m, inc)          (Eq. (5))
+//                FP64: y = y + inc;  FP32-Kahan: s = inc - c; t = y + s; c = (t - y) - s; y = t
+#include <algorithm>
+#include <mutex>
+
+#include "rk4_generic.cuh"
+
+namespace rk4d {
+
+// ---- one-stage-per-launch reference ------------------------------------------------------
+
+template <typename R, int D>
+__global__ void __launch_bounds__(256) k_gen_state(GenStagedJob job, Tableau<R> tb, int j) {
+  const R *Y = static_cast<const R *>(job.y);
+  const R *K = static_cast<const R *>(job.k);
+  R *U = static_cast<R *>(job.u);
+  const size_t plane = (size_t)job.total * D;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < job.total; i += stride) {
+    R y[D], k[kMaxStages][D], u[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) y[d] = Y[i * D + d];
+#pragma unroll
+    for (int m = 0; m < kMaxStages; ++m)
+#pragma unroll
+      for (int d = 0; d < D; ++d) k[m][d] = (m < j) ? K[m * plane + i * D + d] : R(0);
+    gen_stage_state<R, D>(j, tb, y, k, u);
+#pragma unroll
+    for (int d = 0; d < D; ++d) U[i * D + d] = u[d];
+  }
+}
+
+template <typename R, int MODEL, int RANGE>
+__global__ void __launch_bounds__(256) k_gen_slope(GenStagedJob job, Coef<R> cf, R kappa2, int j) {
+  constexpr int D = Dim<MODEL>::D;
+  const R *src = static_cast<const R *>(j == 0 ? job.y : job.u);
+  R *K = static_cast<R *>(job.k) + (size_t)j * job.total * D;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < job.total; i += stride) {
+    ChainDesc ch;
+    Coef<R> c = cf;
+    if (job.nchains == 1) {
+      ch = job.one;
+    } else {
+      int lo = 0, hi = job.nchains - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (job.chains[mid].off <= i) lo = mid; else hi = mid - 1;
+      }
+      ch = job.chains[lo];
+      c.kappa = (R)ch.kappa;
+    }
+    const int64_t li = i - ch.off;
+    auto xat = [&](int64_t q) -> R {  // coupling coordinate of chain site q (boundary-resolved)
+      if (ch.bc == PERIODIC) return src[(ch.off + wrap(q, ch.n)) * D];
+      return (q < 0 || q >= ch.n) ? R(0) : src[(ch.off + q) * D];
+    };
+    R u[D], k[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) u[d] = src[i * D + d];
+    slope_gen<R, MODEL, RANGE>(u, xat(li - 1), xat(li + 1), RANGE == 2 ? xat(li - 2) : R(0),
+                               RANGE == 2 ? xat(li + 2) : R(0), c, kappa2, k);
+#pragma unroll
+    for (int d = 0; d < D; ++d) K[i * D + d] = k[d];
+  }
+}
+
+template <typename R, int D, bool KAHAN>
+__global__ void __launch_bounds__(256) k_gen_combine(GenStagedJob job, Tableau<R> tb) {
+  R *Y = static_cast<R *>(job.y);
+  R *CMP = static_cast<R *>(job.cmp);
+  const R *K = static_cast<const R *>(job.k);
+  const size_t plane = (size_t)job.total * D;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < job.total; i += stride) {
+    R y[D], k[kMaxStages][D], cmp[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      y[d] = Y[i * D + d];
+      cmp[d] = KAHAN ? CMP[i * D + d] : R(0);
+    }
+#pragma unroll
+    for (int m = 0; m < kMaxStages; ++m)
+#pragma unroll
+      for (int d = 0; d < D; ++d) k[m][d] = (m < tb.s) ? K[m * plane + i * D + d] : R(0);
+    gen_combine<R, D, KAHAN>(tb, k, y, cmp);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      Y[i * D + d] = y[d];
+      if constexpr (KAHAN) CMP[i * D + d] = cmp[d];
+    }
+  }
+}
+
+// ---- temporally blocked generic kernel ----------------------------------------------------
+
+// Advance one tile's registers K steps of the generic scheme.  `edge`: 2 parities x 4 slots x
+// 32 warps = 256 values of shared memory (slots: first two and last two coupling coordinates
+// of each warp).
+template <typename R, int MODEL, int V, int RANGE, bool KAHAN, bool MASK>
+__device__ __forceinline__ void gen_tile_advance(R (&y)[V][Dim<MODEL>::D], R (&cmp)[V][Dim<MODEL>::D],
+                                                 uint32_t ghost, int K, const Coef<R> &cf, R kappa2,
+                                                 const Tableau<R> &tb, R *edge) {
+  constexpr int D = Dim<MODEL>::D;
+  static_assert(RANGE == 1 || V >= 2, "second-neighbour coupling needs two sites per thread");
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  const bool is_first = lane == 0, is_last = lane == 31;
+  const int prev = (warp > 0) ? warp - 1 : warp;
+  const int next = (warp < nw - 1) ? warp + 1 : warp;
+  R k[V][kMaxStages][D];
+
+  int parity = 0;  // edge slots alternate strictly from stage to stage (s may be odd)
+#pragma unroll 1
+  for (int s = 0; s < K; ++s) {
+#pragma unroll
+    for (int j = 0; j < kMaxStages; ++j) {
+      if (j >= tb.s) break;
+      R u[V][D];
+      R ext[V + 4];  // ext[2 + v] = x of site v; two neighbours on each side
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        gen_stage_state<R, D>(j, tb, y[v], k[v], u[v]);
+        ext[2 + v] = (MASK && ((ghost >> v) & 1u)) ? R(0) : u[v][0];
+      }
+      ext[1] = __shfl_up_sync(kFull, ext[V + 1], 1);
+      ext[V + 2] = __shfl_down_sync(kFull, ext[2], 1);
+      if constexpr (RANGE == 2) {
+        ext[0] = __shfl_up_sync(kFull, ext[V], 1);
+        ext[V + 3] = __shfl_down_sync(kFull, ext[3], 1);
+      }
+      R *eb = edge + parity * 128;  // [0,32) first x, [32,64) second x, [64,96) last x, [96,128) second-last
+      parity ^= 1;
+      st_shared_if(is_first, eb + warp, ext[2]);
+      st_shared_if(is_last, eb + 64 + warp, ext[V + 1]);
+      if constexpr (RANGE == 2) {
+        st_shared_if(is_first, eb + 32 + warp, ext[3]);
+        st_shared_if(is_last, eb + 96 + warp, ext[V]);
+      }
+      __syncthreads();
+      {
+        const R p1 = eb[64 + prev], n1 = eb[next];
+        ext[1] = is_first ? p1 : ext[1];
+        ext[V + 2] = is_last ? n1 : ext[V + 2];
+        if constexpr (RANGE == 2) {
+          const R p2 = eb[96 + prev], n2 = eb[32 + next];
+          ext[0] = is_first ? p2 : ext[0];
+          ext[V + 3] = is_last ? n2 : ext[V + 3];
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        R kv[D];
+        slope_gen<R, MODEL, RANGE>(u[v], ext[1 + v], ext[3 + v], RANGE == 2 ? ext[v] : R(0),
+                                   RANGE == 2 ? ext[4 + v] : R(0), cf, kappa2, kv);
+#pragma unroll
+        for (int d = 0; d < D; ++d) k[v][j][d] = kv[d];
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) gen_combine<R, D, KAHAN>(tb, k[v], y[v], cmp[v]);
+  }
+}
+
+template <typename R, int MODEL, int V, int RANGE, bool KAHAN>
+__global__ void __launch_bounds__(gen_max_threads(V)) k_gen_blocked(BlockedJob job, Coef<R> cf, R kappa2,
+                                                                     Tableau<R> tb, int H) {
+  constexpr int D = Dim<MODEL>::D;
+  extern __shared__ __align__(16) unsigned char smem[];
+  R *edge = reinterpret_cast<R *>(smem);
+  R *tl = edge + 256;
+  const int W = blockDim.x * V;
+  R *ctl = tl + W * D;
+  const int64_t item = blockIdx.x;
+  ChainDesc ch;
+  int64_t tile = item;
+  Coef<R> c = cf;
+  if (job.nchains == 1) {
+    ch = job.one;
+  } else {
+    const int ci = find_chain(job.tile_prefix, job.nchains, item);
+    ch = job.chains[ci];
+    tile = item - job.tile_prefix[ci];
+    c.kappa = (R)ch.kappa;
+  }
+  const int G = job.G;
+  const int64_t t0 = tile * (int64_t)G - H;
+  tile_load<R, D, false>(tl, static_cast<const R *>(job.in), ch.off, ch.n, ch.bc, t0, W);
+  if constexpr (KAHAN) tile_load<R, D, false>(ctl, static_cast<const R *>(job.cin), ch.off, ch.n, ch.bc, t0, W);
+  __syncthreads();
+  R y[V][D], cmp[V][D];
+  const int base = threadIdx.x * V;
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      y[v][d] = tl[(base + v) * D + d];
+      if constexpr (KAHAN) cmp[v][d] = ctl[(base + v) * D + d]; else cmp[v][d] = R(0);
+    }
+  const bool edge_tile = (ch.bc == FIXED) && (t0 < 0 || t0 + W > ch.n);
+  if (edge_tile) {
+    uint32_t ghost = 0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int64_t g = t0 + base + v;
+      if (g < 0 || g >= ch.n) ghost |= 1u << v;
+    }
+    gen_tile_advance<R, MODEL, V, RANGE, KAHAN, true>(y, cmp, ghost, job.K, c, kappa2, tb, edge);
+  } else {
+    gen_tile_advance<R, MODEL, V, RANGE, KAHAN, false>(y, cmp, 0u, job.K, c, kappa2, tb, edge);
+  }
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      tl[(base + v) * D + d] = y[v][d];
+      if constexpr (KAHAN) ctl[(base + v) * D + d] = cmp[v][d];
+    }
+  __syncthreads();
+  const int64_t g0 = t0 + H;
+  const int64_t rem = ch.n - g0;
+  const int cnt = (int)(rem < G ? rem : G);
+  if (cnt > 0) {
+    tile_store<R, D>(static_cast<R *>(job.out), tl, ch.off, H, g0, cnt);
+    if constexpr (KAHAN) tile_store<R, D>(static_cast<R *>(job.cout), ctl, ch.off, H, g0, cnt);
+  }
+}
+
+template <typename R, int MODEL, int V, int RANGE, bool KAHAN>
+static int gen_max_threads_one() {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, k_gen_blocked<R, MODEL, V, RANGE, KAHAN>) != cudaSuccess) return 0;
+  return a.maxThreadsPerBlock;
+}
+
+template <int MODEL, int RANGE>
+static int gen_max_threads_m(bool fp32, int v) {
+  if (v == 2) return fp32 ? gen_max_threads_one<float, MODEL, 2, RANGE, true>() : gen_max_threads_one<double, MODEL, 2, RANGE, false>();
+  if (v == 4) return fp32 ? gen_max_threads_one<float, MODEL, 4, RANGE, true>() : gen_max_threads_one<double, MODEL, 4, RANGE, false>();
+  return 0;
+}
+
+int gen_blocked_max_threads(int model, bool fp32, int range, int v) {
+  if (model == ROESSLER) return range == 1 ? gen_max_threads_m<ROESSLER, 1>(fp32, v) : gen_max_threads_m<ROESSLER, 2>(fp32, v);
+  return range == 1 ? gen_max_threads_m<HARMONIC, 1>(fp32, v) : gen_max_threads_m<HARMONIC, 2>(fp32, v);
+}
+
+size_t gen_blocked_smem_bytes(int model, bool fp32, int v, int block) {
+  const int D = model == ROESSLER ? 3 : 2;
+  const size_t rs = fp32 ? 4 : 8;
+  return 256 * rs + (size_t)block * v * D * rs * (fp32 ? 2 : 1);
+}
+
+// ---- launchers ------------------------------------------------------------------------------
+
+template <typename R>
+static Tableau<R> to_tableau(const TableauD &t, double dt) {
+  Tableau<R> r{};
+  r.s = t.s;
+  for (int j = 0; j < kMaxStages; ++j) {
+    r.anz[j] = 0;
+    for (int m = 0; m < kMaxStages; ++m) {
+      const double a = (j < t.s && m < j) ? t.a[j][m] : 0.0;
+      r.adt[j][m] = (R)(a * dt);
+      if (a != 0.0) r.anz[j] |= 1u << m;
+    }
+  }
+  r.bnz = 0;
+  for (int m = 0; m < kMaxStages; ++m) {
+    const double b = m < t.s ? t.b[m] : 0.0;
+    r.bdt[m] = (R)(b * dt);
+    if (b != 0.0) r.bnz |= 1u << m;
+  }
+  return r;
+}
+
+static int64_t staged_grid(int64_t total) {
+  int64_t g = (total + 255) / 256;
+  return g > 152 * 64 ? 152 * 64 : (g < 1 ? 1 : g);
+}
+
+template <typename R, int MODEL, int RANGE, bool KAHAN>
+static cudaError_t gen_staged_t(const GenStagedJob &job, const CoefD &cfd, const TableauD &td, double dt,
+                                cudaStream_t st) {
+  constexpr int D = Dim<MODEL>::D;
+  if (job.total <= 0) return cudaSuccess;
+  const Tableau<R> tb = to_tableau<R>(td, dt);
+  const Coef<R> cf = to_coef<R>(cfd, cfd.kappa);
+  const unsigned grid = (unsigned)staged_grid(job.total);
+  for (int j = 0; j < td.s; ++j) {
+    if (j > 0) k_gen_state<R, D><<<grid, 256, 0, st>>>(job, tb, j);
+    k_gen_slope<R, MODEL, RANGE><<<grid, 256, 0, st>>>(job, cf, (R)cfd.kappa2, j);
+  }
+  k_gen_combine<R, D, KAHAN><<<grid, 256, 0, st>>>(job, tb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gen_staged_step(int model, bool fp32, int range, const GenStagedJob &job, const CoefD &cf,
+                                   const TableauD &tb, double dt, cudaStream_t st) {
+#define RK4_GEN_STAGED(MODEL)                                                                            \
+  if (range == 1)                                                                                        \
+    return fp32 ? gen_staged_t<float, MODEL, 1, true>(job, cf, tb, dt, st)                              \
+                : gen_staged_t<double, MODEL, 1, false>(job, cf, tb, dt, st);                            \
+  return fp32 ? gen_staged_t<float, MODEL, 2, true>(job, cf, tb, dt, st)                                 \
+              : gen_staged_t<double, MODEL, 2, false>(job, cf, tb, dt, st);
+  if (model == ROESSLER) {
+    RK4_GEN_STAGED(ROESSLER)
+  }
+  RK4_GEN_STAGED(HARMONIC)
+#undef RK4_GEN_STAGED
+}
+
+template <typename R, int MODEL, int V, int RANGE, bool KAHAN>
+static cudaError_t gen_blocked_t(int block, const BlockedJob &job, const CoefD &cfd, const TableauD &td, double dt,
+                                 int H, cudaStream_t st) {
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(k_gen_blocked<R, MODEL, V, RANGE, KAHAN>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  if (job.ntiles <= 0) return cudaSuccess;
+  const size_t smem = gen_blocked_smem_bytes(MODEL, KAHAN, V, block);
+  k_gen_blocked<R, MODEL, V, RANGE, KAHAN><<<(unsigned)job.ntiles, block, smem, st>>>(
+      job, to_coef<R>(cfd, cfd.kappa), (R)cfd.kappa2, to_tableau<R>(td, dt), H);
+  return cudaGetLastError();
+}
+
+template <int MODEL, int RANGE>
+static cudaError_t gen_blocked_m(bool fp32, int v, int block, const BlockedJob &job, const CoefD &cf,
+                                 const TableauD &tb, double dt, int H, cudaStream_t st) {
+  switch (v) {
+    case 2:
+      return fp32 ? gen_blocked_t<float, MODEL, 2, RANGE, true>(block, job, cf, tb, dt, H, st)
+                  : gen_blocked_t<double, MODEL, 2, RANGE, false>(block, job, cf, tb, dt, H, st);
+    case 4:
+      return fp32 ? gen_blocked_t<float, MODEL, 4, RANGE, true>(block, job, cf, tb, dt, H, st)
+                  : gen_blocked_t<double, MODEL, 4, RANGE, false>(block, job, cf, tb, dt, H, st);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_gen_blocked(int model, bool fp32, int range, int v, int block, const BlockedJob &job,
+                               const CoefD &cf, const TableauD &tb, double dt, int H, cudaStream_t st) {
+  if (model == ROESSLER)
+    return range == 1 ? gen_blocked_m<ROESSLER, 1>(fp32, v, block, job, cf, tb, dt, H, st)
+                      : gen_blocked_m<ROESSLER, 2>(fp32, v, block, job, cf, tb, dt, H, st);
+  return range == 1 ? gen_blocked_m<HARMONIC, 1>(fp32, v, block, job, cf, tb, dt, H, st)
+                    : gen_blocked_m<HARMONIC, 2>(fp32, v, block, job, cf, tb, dt, H, st);
+}
+
+}  // namespace rk4d

@@ -18,8 +18,8 @@ __device__ __forceinline__ double site_value(const R *y, const R *c, int64_t idx
 // Energy contribution of site i (chain-local) plus its bond to the right neighbour; the left
 // ghost bond of a fixed chain is added at i == 0.
 template <int MODEL, typename R>
-__device__ __forceinline__ double site_energy(const R *y, const R *c, const ChainDesc &ch, double w2, int64_t i,
-                                              bool &bad) {
+__device__ __forceinline__ double site_energy(const R *y, const R *c, const ChainDesc &ch, double w2, double kappa2,
+                                              int64_t i, bool &bad) {
   constexpr int D = Dim<MODEL>::D;
   const int64_t g = ch.off + i;
   if constexpr (MODEL == ROESSLER) {
@@ -36,6 +36,14 @@ __device__ __forceinline__ double site_energy(const R *y, const R *c, const Chai
     const double dq = qr - q;
     double e = 0.5 * p * p + 0.5 * w2 * q * q + 0.5 * ch.kappa * dq * dq;
     if (i == 0 && ch.bc == FIXED) e += 0.5 * ch.kappa * q * q;
+    if (kappa2 != 0.0) {  // second-neighbour bonds (i, i+2), and the ghost bonds ending at sites 0, 1
+      double q2;
+      if (i + 2 < ch.n) q2 = site_value<MODEL>(y, c, (g + 2) * D);
+      else q2 = (ch.bc == PERIODIC) ? site_value<MODEL>(y, c, (ch.off + (i + 2) % ch.n) * D) : 0.0;
+      const double d2 = q2 - q;
+      e += 0.5 * kappa2 * d2 * d2;
+      if (i < 2 && ch.bc == FIXED) e += 0.5 * kappa2 * q * q;
+    }
     return e;
   }
 }
@@ -55,13 +63,13 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 
 template <int MODEL, typename R>
 __global__ void __launch_bounds__(256) k_energy_chain(const R *y, const R *c, ChainDesc ch, double w2,
-                                                      double *partials, WsHeader *hdr) {
+                                                      double kappa2, double *partials, WsHeader *hdr) {
   __shared__ double red[32];
   bool bad = false;
   double acc = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ch.n; i += stride)
-    acc += site_energy<MODEL>(y, c, ch, w2, i, bad);
+    acc += site_energy<MODEL>(y, c, ch, w2, kappa2, i, bad);
   if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(&hdr->status, ST_NONFINITE);
   const double s = block_sum(acc, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
@@ -78,12 +86,12 @@ __global__ void __launch_bounds__(1024) k_energy_final(const double *partials, i
 // One block per chain of a batch.
 template <int MODEL, typename R>
 __global__ void __launch_bounds__(256) k_energy_batch(const R *y, const R *c, const ChainDesc *chains, double w2,
-                                                      double *out, WsHeader *hdr) {
+                                                      double kappa2, double *out, WsHeader *hdr) {
   __shared__ double red[32];
   const ChainDesc ch = chains[blockIdx.x];
   bool bad = false;
   double acc = 0.0;
-  for (int64_t i = threadIdx.x; i < ch.n; i += blockDim.x) acc += site_energy<MODEL>(y, c, ch, w2, i, bad);
+  for (int64_t i = threadIdx.x; i < ch.n; i += blockDim.x) acc += site_energy<MODEL>(y, c, ch, w2, kappa2, i, bad);
   if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(&hdr->status, ST_NONFINITE);
   const double s = block_sum(acc, red);
   if (threadIdx.x == 0) out[blockIdx.x] = s;
@@ -96,10 +104,10 @@ static cudaError_t energy_t(const void *state, const void *cmp, int nchains, con
   const R *y = static_cast<const R *>(state);
   const R *c = static_cast<const R *>(cmp);
   if (nchains == 1) {
-    k_energy_chain<MODEL, R><<<kEnergyBlocks, 256, 0, st>>>(y, c, one, cf.w2, partials, hdr);
+    k_energy_chain<MODEL, R><<<kEnergyBlocks, 256, 0, st>>>(y, c, one, cf.w2, cf.kappa2, partials, hdr);
     k_energy_final<<<1, 1024, 0, st>>>(partials, kEnergyBlocks, out);
   } else {
-    k_energy_batch<MODEL, R><<<nchains, 256, 0, st>>>(y, c, chains, cf.w2, out, hdr);
+    k_energy_batch<MODEL, R><<<nchains, 256, 0, st>>>(y, c, chains, cf.w2, cf.kappa2, out, hdr);
   }
   return cudaGetLastError();
 }

@@ -72,20 +72,48 @@ struct rk4_chain {
   size_t tables_bytes = 0;
   std::vector<int> tables_k;  // the k values the prefix arrays currently describe
   int tables_W = 0;           // and the tile width they were computed for
+  int tables_halo = 0;        // and the halo per step
   double *h_out = nullptr;    // pinned: reduction results (nchains doubles)
   int *h_status = nullptr;    // pinned: status word read-back
   GraphKey gkey;
   cudaGraphExec_t gexec = nullptr;
+  // generic explicit RK scheme (any tableau, coupling range 1 or 2)
+  bool has_tableau = false;
+  TableauD tab{};
+  double kappa2 = 0.0;
 };
 
 namespace {
 
+bool use_generic(const rk4_chain *h);
+
 int effective_kernel(const rk4_chain *h) {
   if (h->kernel != RK4_KERNEL_AUTO) return h->kernel;
-  return h->nchains == 1 ? RK4_KERNEL_BLOCKED : RK4_KERNEL_PERSISTENT;
+  return (h->nchains == 1 || use_generic(h)) ? RK4_KERNEL_BLOCKED : RK4_KERNEL_PERSISTENT;
 }
 
 size_t elem_bytes(const rk4_chain *h) { return h->fp32 ? 4 : 8; }
+
+// The generic kernels run when a tableau was set or second-neighbour coupling is on.
+bool use_generic(const rk4_chain *h) { return h->has_tableau || h->kappa2 != 0.0; }
+int coupling_range(const rk4_chain *h) { return h->kappa2 != 0.0 ? 2 : 1; }
+int stages(const rk4_chain *h) { return use_generic(h) ? h->tab.s : 4; }
+
+// Halo per side of one launch of k steps: s stages, each reaching `range` sites further.
+int halo(const rk4_chain *h, int k) { return stages(h) * coupling_range(h) * k; }
+
+TableauD classical_rk4() {
+  TableauD t{};
+  t.s = 4;
+  t.a[1][0] = 0.5;
+  t.a[2][1] = 0.5;
+  t.a[3][2] = 1.0;
+  t.b[0] = 1.0 / 6.0;
+  t.b[1] = 1.0 / 3.0;
+  t.b[2] = 1.0 / 3.0;
+  t.b[3] = 1.0 / 6.0;
+  return t;
+}
 
 WsLayout layout(const rk4_chain *h, int kernel) {
   WsLayout L{};
@@ -102,7 +130,10 @@ WsLayout layout(const rk4_chain *h, int kernel) {
   L.prefix = take(h->nchains > 1 ? sizeof(int32_t) * (size_t)(h->nchains + 1) * kMaxDistinctK : 0);
   const size_t sz = (size_t)h->total * (size_t)h->D * elem_bytes(h);
   L.state = L.comp = L.u0 = L.u1 = L.acc = 0;
-  if (kernel == RK4_KERNEL_STAGED) {
+  if (kernel == RK4_KERNEL_STAGED && use_generic(h)) {
+    L.u0 = take(sz);                     // stage state
+    L.acc = take(sz * (size_t)h->tab.s);  // the s stage slopes
+  } else if (kernel == RK4_KERNEL_STAGED) {
     L.u0 = take(sz);
     L.u1 = take(sz);
     L.acc = take(sz);
@@ -124,17 +155,30 @@ CoefD coef(const rk4_chain *h) {
   c.h2 = h->dt / 2.0;
   c.h1 = h->dt;
   c.dt6 = h->dt / 6.0;
+  c.kappa2 = h->kappa2;
   return c;
 }
 
 int tiling_valid(const rk4_chain *h, int block, int v, int k) {
   if (block < 64 || block > 1024 || (block % 32) != 0) return 0;
-  if (v != 1 && v != 2 && v != 4 && v != 8) return 0;
   if (k < 1 || k > 16) return 0;
   const int W = block * v;
+  if (use_generic(h)) {
+    if (v != 2 && v != 4) return 0;
+    const int H = halo(h, k);
+    if (W - 2 * H < H) return 0;
+    if (gen_blocked_smem_bytes(h->model, h->fp32, v, block) > kMaxSmem) return 0;
+    return 1;
+  }
+  if (v != 1 && v != 2 && v != 4 && v != 8) return 0;
   if (W - 8 * k < 8 * k) return 0;
   if (blocked_smem_bytes(h->model, h->fp32, v, block) > kMaxSmem) return 0;
   return 1;
+}
+
+int tiling_max_threads(const rk4_chain *h, int v) {
+  return use_generic(h) ? gen_blocked_max_threads(h->model, h->fp32, coupling_range(h), v)
+                        : blocked_max_threads(h->model, h->fp32, v);
 }
 
 void default_tiling(rk4_chain *h) {
@@ -142,10 +186,16 @@ void default_tiling(rk4_chain *h) {
   // cluster from the cache; here a tile should fill a block's registers): FP64 is bound by
   // the FP64 pipe, so k = 1 keeps the redundant halo work minimal; FP32 is bandwidth-bound
   // at k = 1, so several steps per launch pay off.
-  h->tiling.block = 256;
-  h->tiling.v = 4;
-  h->tiling.k = h->fp32 ? 4 : 1;
-  h->tiling.G = h->tiling.block * h->tiling.v - 8 * h->tiling.k;
+  if (use_generic(h)) {
+    h->tiling.block = 128;
+    h->tiling.v = 2;
+    h->tiling.k = 1;
+  } else {
+    h->tiling.block = 256;
+    h->tiling.v = 4;
+    h->tiling.k = h->fp32 ? 4 : 1;
+  }
+  h->tiling.G = h->tiling.block * h->tiling.v - 2 * halo(h, h->tiling.k);
 }
 
 int64_t tiles_for(const rk4_chain *h, int G) {
@@ -210,13 +260,13 @@ cudaError_t ensure_pinned(rk4_chain *h) {
 // Fill the pinned tile-prefix arrays for the plan's k values (waits for earlier uses first).
 cudaError_t prepare_tables(rk4_chain *h, const std::vector<int> &kval, int W) {
   if (h->nchains == 1) return cudaSuccess;
-  if (h->tables_k == kval && h->tables_W == W) return cudaSuccess;
+  if (h->tables_k == kval && h->tables_W == W && h->tables_halo == halo(h, 1)) return cudaSuccess;
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return e;
   int32_t *pre = reinterpret_cast<int32_t *>(static_cast<char *>(h->h_tables) +
                                              align_up(sizeof(ChainDesc) * (size_t)h->nchains));
   for (size_t i = 0; i < kval.size(); ++i) {
-    const int G = W - 8 * kval[i];
+    const int G = W - 2 * halo(h, kval[i]);
     int64_t acc = 0;
     int32_t *p = pre + i * (size_t)(h->nchains + 1);
     for (int c = 0; c < h->nchains; ++c) {
@@ -227,6 +277,7 @@ cudaError_t prepare_tables(rk4_chain *h, const std::vector<int> &kval, int W) {
   }
   h->tables_k = kval;
   h->tables_W = W;
+  h->tables_halo = halo(h, 1);
   return cudaSuccess;
 }
 
@@ -250,6 +301,22 @@ cudaError_t enqueue_integrate(rk4_chain *h, int kernel, void *state, void *comp,
   e = upload_tables(h, ws, L, st);
   if (e != cudaSuccess) return e;
   const size_t bytes = (size_t)h->total * h->D * elem_bytes(h);
+  if (kernel == RK4_KERNEL_STAGED && use_generic(h)) {
+    GenStagedJob j{};
+    j.y = state;
+    j.cmp = comp;
+    j.u = ws + L.u0;
+    j.k = ws + L.acc;
+    j.nchains = h->nchains;
+    j.one = h->chains[0];
+    j.chains = dev_chains(h, ws, L);
+    j.total = h->total;
+    for (int64_t s = 0; s < nsteps; ++s) {
+      e = launch_gen_staged_step(h->model, h->fp32, coupling_range(h), j, cf, h->tab, h->dt, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   if (kernel == RK4_KERNEL_STAGED) {
     StagedJob j{};
     j.y = state;
@@ -284,7 +351,7 @@ cudaError_t enqueue_integrate(rk4_chain *h, int kernel, void *state, void *comp,
       int ki = 0;
       while (P.kval[ki] != k) ++ki;
       j.K = k;
-      j.G = W - 8 * k;
+      j.G = W - 2 * halo(h, k);
       j.ntiles = tiles_for(h, j.G);
       j.tile_prefix = pre ? pre + (size_t)ki * (h->nchains + 1) : nullptr;
       const bool even = (i % 2) == 0;
@@ -292,7 +359,11 @@ cudaError_t enqueue_integrate(rk4_chain *h, int kernel, void *state, void *comp,
       j.out = even ? wsS : state;
       j.cin = even ? comp : wsC;
       j.cout = even ? wsC : comp;
-      e = launch_blocked(h->model, h->fp32, h->tiling.v, h->tiling.block, j, cf, st);
+      if (use_generic(h))
+        e = launch_gen_blocked(h->model, h->fp32, coupling_range(h), h->tiling.v, h->tiling.block, j, cf, h->tab,
+                               h->dt, halo(h, k), st);
+      else
+        e = launch_blocked(h->model, h->fp32, h->tiling.v, h->tiling.block, j, cf, st);
       if (e != cudaSuccess) return e;
     }
   } else {  // persistent
@@ -347,6 +418,7 @@ int integrate_impl(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_by
   if (rc) return rc;
   if (nsteps < 0) return RK4_EINVAL;
   const int kernel = effective_kernel(h);
+  if (kernel == RK4_KERNEL_PERSISTENT && use_generic(h)) return RK4_EUNSUPPORTED;
   const WsLayout L = layout(h, kernel);
   if (ws_bytes < L.total) return RK4_ENOMEM_WS;
   if (nsteps == 0) return RK4_OK;
@@ -356,7 +428,7 @@ int integrate_impl(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_by
   if (kernel != RK4_KERNEL_STAGED) {
     // tile counts must fit a 1-D grid and the int32 prefix tables
     const int kmax = *std::max_element(P.kval.begin(), P.kval.end());
-    if (tiles_for(h, h->tiling.block * h->tiling.v - 8 * kmax) > 0x7fffffffLL) return RK4_EUNSUPPORTED;
+    if (tiles_for(h, h->tiling.block * h->tiling.v - 2 * halo(h, kmax)) > 0x7fffffffLL) return RK4_EUNSUPPORTED;
   }
   if (prepare_tables(h, P.kval, h->tiling.block * h->tiling.v) != cudaSuccess) return RK4_ECUDA;
   char *w = static_cast<char *>(ws);
@@ -422,6 +494,7 @@ rk4_chain *new_handle(int model, int precision, double dt, const rk4_params *p, 
   h->dt = dt;
   if (p) h->p = *p; else rk4_params_default(&h->p);
   h->stream = static_cast<cudaStream_t>(stream);
+  h->tab = classical_rk4();
   default_tiling(h);
   return h;
 }
@@ -533,13 +606,13 @@ int rk4_chain_set_tiling(rk4_chain *h, int block, int v, int k) {
     return RK4_OK;
   }
   if (!tiling_valid(h, block, v, k)) return RK4_EINVAL;
-  const int maxt = blocked_max_threads(h->model, h->fp32, v);
+  const int maxt = tiling_max_threads(h, v);
   if (maxt > 0 && block > maxt) return RK4_EINVAL;
   h->tiling_auto = false;
   h->tiling.block = block;
   h->tiling.v = v;
   h->tiling.k = k;
-  h->tiling.G = block * v - 8 * k;
+  h->tiling.G = block * v - 2 * halo(h, k);
   return RK4_OK;
 }
 
@@ -662,6 +735,7 @@ int rk4_debug_barrier_timeout(rk4_chain *h, void *state, void *comp, void *ws, s
   j.tile_prefix = h->nchains > 1 ? reinterpret_cast<const int32_t *>(w + L.prefix) : nullptr;
   j.nk = 1;
   j.kval[0] = h->tiling.k;
+  if (use_generic(h)) return RK4_EUNSUPPORTED;
   j.Gval[0] = W - 8 * h->tiling.k;
   j.ntiles[0] = tiles_for(h, j.Gval[0]);
   j.nmain = 1;
@@ -698,7 +772,7 @@ int rk4_chain_autotune(rk4_chain *h, void *state, void *comp, void *ws, size_t w
     h->graphs = saved_graphs;
     return RK4_ECUDA;
   }
-  static const int blocks[] = {128, 256, 512, 1024};
+  static const int blocks[] = {64, 128, 256, 512, 1024};
   static const int vs[] = {1, 2, 4, 8};
   static const int ks[] = {1, 2, 4, 8, 16};
   float best_ms = 1e30f;
@@ -708,13 +782,14 @@ int rk4_chain_autotune(rk4_chain *h, void *state, void *comp, void *ws, size_t w
     for (int v : vs)
       for (int k : ks) {
         if (!tiling_valid(h, b, v, k)) continue;
-        const int maxt = blocked_max_threads(h->model, h->fp32, v);
+        if (b == 64 && !use_generic(h)) continue;
+        const int maxt = tiling_max_threads(h, v);
         if (maxt <= 0 || b > maxt) continue;
         if (kernel == RK4_KERNEL_PERSISTENT && persistent_max_grid(h->model, h->fp32, v, b) <= 0) continue;
         h->tiling.block = b;
         h->tiling.v = v;
         h->tiling.k = k;
-        h->tiling.G = b * v - 8 * k;
+        h->tiling.G = b * v - 2 * halo(h, k);
         const int64_t steps = ((probe_steps + 2 * k - 1) / (2 * k)) * 2 * k;  // whole, even launch count
         if (integrate_impl(h, state, comp, ws, ws_bytes, 2 * k) != RK4_OK) continue;  // warm-up
         cudaEventRecord(e0, h->stream);
@@ -742,6 +817,41 @@ int rk4_chain_autotune(rk4_chain *h, void *state, void *comp, void *ws, size_t w
   h->tiling = best_t;
   h->tiling_auto = false;
   if (best) *best = best_t;
+  return RK4_OK;
+}
+
+int rk4_chain_set_tableau(rk4_chain *h, int s, const double *A, const double *b) {
+  if (!h) return RK4_EINVAL;
+  if (s == 0) {  // back to the classical RK4 kernels
+    h->has_tableau = false;
+    h->tab = classical_rk4();
+    default_tiling(h);
+    return RK4_OK;
+  }
+  if (s < 1 || s > kMaxStages || !A || !b) return RK4_EINVAL;
+  TableauD t{};
+  t.s = s;
+  for (int j = 0; j < s; ++j) {
+    if (!std::isfinite(b[j])) return RK4_EINVAL;
+    t.b[j] = b[j];
+    for (int m = 0; m < s; ++m) {
+      const double a = A[j * s + m];
+      if (!std::isfinite(a)) return RK4_EINVAL;
+      if (m >= j && a != 0.0) return RK4_EINVAL;  // explicit schemes only
+      if (m < j) t.a[j][m] = a;
+    }
+  }
+  h->has_tableau = true;
+  h->tab = t;
+  default_tiling(h);
+  return RK4_OK;
+}
+
+int rk4_chain_set_coupling2(rk4_chain *h, double kappa2) {
+  if (!h || !std::isfinite(kappa2)) return RK4_EINVAL;
+  h->kappa2 = kappa2;
+  if (!h->has_tableau) h->tab = classical_rk4();
+  default_tiling(h);
   return RK4_OK;
 }
 

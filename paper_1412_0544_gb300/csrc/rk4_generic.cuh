@@ -1,0 +1,78 @@
+// rk4_generic.cuh -- per-site arithmetic of the generic explicit Runge-Kutta scheme (any
+// tableau of up to kMaxStages stages, coupling range 1 or 2).  Shared by the staged and the
+// blocked generic kernels so that both perform the same operations in the same order.
+#pragma once
+#include "rk4_tile.cuh"
+
+namespace rk4d {
+
+// Largest block of the generic tile kernel by sites per thread (it keeps every stage slope
+// of every site in registers).
+__host__ __device__ constexpr int gen_max_threads(int v) { return v <= 2 ? 256 : 128; }
+
+// The tableau in the working precision: a_jm dt and b_m dt rounded once on the host, plus
+// bit masks of the nonzero entries (zero entries are skipped, in every kernel alike).
+template <typename R> struct Tableau {
+  int s;
+  R adt[kMaxStages][kMaxStages];
+  R bdt[kMaxStages];
+  uint32_t anz[kMaxStages];
+  uint32_t bnz;
+};
+
+// Eq. (4): stage state of stage j from the step's start y and the earlier slopes.
+template <typename R, int D>
+__device__ __forceinline__ void gen_stage_state(int j, const Tableau<R> &tb, const R *y, const R (*k)[D], R *u) {
+#pragma unroll
+  for (int d = 0; d < D; ++d) u[d] = y[d];
+#pragma unroll
+  for (int m = 0; m < kMaxStages; ++m) {
+    if (m < j && ((tb.anz[j] >> m) & 1u)) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) u[d] = fma(tb.adt[j][m], k[m][d], u[d]);
+    }
+  }
+}
+
+// Eq. (3) with coupling range 1 (the RK4 kernels' slope) or 2 (second neighbours added
+// inside the coupling term).
+template <typename R, int MODEL, int RANGE>
+__device__ __forceinline__ void slope_gen(const R *u, R xl, R xr, R xl2, R xr2, const Coef<R> &cf, R kappa2,
+                                          R *k) {
+  if constexpr (RANGE == 1) {
+    slope<R, MODEL>(u, xl, xr, cf, k);
+  } else {
+    const R lap = fma(R(-2), u[0], add(xl, xr));
+    const R lap2 = fma(R(-2), u[0], add(xl2, xr2));
+    if constexpr (MODEL == ROESSLER) {
+      k[0] = fma(cf.kappa, lap, fma(kappa2, lap2, -add(u[1], u[2])));
+      k[1] = fma(cf.a, u[1], u[0]);
+      k[2] = fma(u[2], sub(u[0], cf.c), cf.b);
+    } else {
+      k[0] = u[1];
+      k[1] = fma(cf.kappa, lap, fma(kappa2, lap2, -mul(cf.w2, u[0])));
+    }
+  }
+}
+
+// Eq. (5): y += sum_m b_m dt k_m, in FP64 or with a Kahan-compensated update in FP32.
+template <typename R, int D, bool KAHAN>
+__device__ __forceinline__ void gen_combine(const Tableau<R> &tb, const R (*k)[D], R *y, R *cmp) {
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    R inc = R(0);
+#pragma unroll
+    for (int m = 0; m < kMaxStages; ++m)
+      if (m < tb.s && ((tb.bnz >> m) & 1u)) inc = fma(tb.bdt[m], k[m][d], inc);
+    if constexpr (KAHAN) {
+      const R s = sub(inc, cmp[d]);
+      const R t = add(y[d], s);
+      cmp[d] = sub(sub(t, y[d]), s);
+      y[d] = t;
+    } else {
+      y[d] = add(y[d], inc);
+    }
+  }
+}
+
+}  // namespace rk4d

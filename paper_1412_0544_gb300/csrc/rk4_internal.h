@@ -17,8 +17,17 @@ struct ChainDesc {
 };
 
 // Coefficients in double; converted to the working precision once per launch on the host.
+// kappa2: second-neighbour coupling (generic scheme only; 0 for the paper's chain).
 struct CoefD {
-  double a, b, c, kappa, w2, h2, h1, dt6;
+  double a, b, c, kappa, w2, h2, h1, dt6, kappa2;
+};
+
+// Generic explicit Runge-Kutta tableau (strictly lower a, weights b), up to kMaxStages stages.
+constexpr int kMaxStages = 7;
+struct TableauD {
+  int s;
+  double a[kMaxStages][kMaxStages];
+  double b[kMaxStages];
 };
 
 // Device status word bits (in the workspace header).
@@ -60,6 +69,19 @@ struct StagedJob {
   int64_t total;             // total sites
 };
 
+// One step of the generic standard scheme: stage states, slopes and the combination, each a
+// full sweep.  k holds s slope arrays of total * D values; u one stage state.
+struct GenStagedJob {
+  void *y;
+  void *cmp;
+  void *u;
+  void *k;
+  int nchains;
+  ChainDesc one;
+  const ChainDesc *chains;
+  int64_t total;
+};
+
 struct PersistentJob {
   void *bufA, *bufB;            // state ping-pong: time block t reads A when t is even
   void *cA, *cB;                // compensation ping-pong (FP32) or NULL
@@ -92,6 +114,12 @@ cudaError_t launch_energy(int model, bool fp32, const void *state, const void *c
                           double *out, WsHeader *hdr, cudaStream_t st);
 cudaError_t launch_fill_uniform(void *dst, int64_t count, uint64_t seed, uint64_t start, bool fp32,
                                 cudaStream_t st);
+cudaError_t launch_gen_staged_step(int model, bool fp32, int range, const GenStagedJob &job, const CoefD &cf,
+                                   const TableauD &tb, double dt, cudaStream_t st);
+cudaError_t launch_gen_blocked(int model, bool fp32, int range, int v, int block, const BlockedJob &job,
+                               const CoefD &cf, const TableauD &tb, double dt, int H, cudaStream_t st);
+size_t gen_blocked_smem_bytes(int model, bool fp32, int v, int block);
+int gen_blocked_max_threads(int model, bool fp32, int range, int v);
 size_t blocked_smem_bytes(int model, bool fp32, int v, int block);
 int blocked_max_threads(int model, bool fp32, int v);
 

@@ -152,3 +152,32 @@ def test_multirank_helpers_gloo(tmp_path):
     assert all(o["max"] == 2.0 and o["sum"] == 30.0 for o in outs)
     a, b = outs[0]["mine"], outs[1]["mine"]
     assert not set(a) & set(b) and sorted(a + b) == list(range(256))
+
+
+def test_generic_scheme_validation(rk):
+    h = rk.rk4_chain_create(0, 0, 1000, 0.01, 0)
+    try:
+        with pytest.raises(rk.RK4Error):  # not explicit: nonzero diagonal
+            rk.rk4_chain_set_tableau(h, np.eye(2), np.array([0.5, 0.5]))
+        with pytest.raises(rk.RK4Error):  # more than 7 stages
+            rk.rk4_chain_set_tableau(h, np.zeros((8, 8)), np.full(8, 1 / 8))
+        with pytest.raises(rk.RK4Error):
+            rk.rk4_chain_set_coupling2(h, float("nan"))
+        A = np.array([[0, 0, 0], [0.5, 0, 0], [-1.0, 2.0, 0]])
+        rk.rk4_chain_set_tableau(h, A, np.array([1 / 6, 2 / 3, 1 / 6]))
+        t = rk.rk4_chain_get_tiling(h)
+        assert t["G"] == t["block"] * t["v"] - 2 * 3 * t["k"]  # halo = s * k per side
+        rk.rk4_chain_set_coupling2(h, 0.5)
+        t = rk.rk4_chain_get_tiling(h)
+        assert t["G"] == t["block"] * t["v"] - 2 * 3 * 2 * t["k"]  # range 2 doubles it
+        with pytest.raises(rk.RK4Error):  # generic kernels have 2 or 4 sites per thread
+            rk.rk4_chain_set_tiling(h, 256, 1, 1)
+        rk.rk4_chain_set_tiling(h, 128, 4, 3)
+        assert rk.rk4_chain_get_tiling(h)["G"] == 512 - 2 * 18
+        rk.rk4_chain_set_kernel(h, rk.RK4_KERNEL_STAGED)
+        assert rk.rk4_chain_workspace_bytes(h) >= 4 * 1000 * 3 * 8  # stage state + 3 slopes
+        rk.rk4_chain_set_tableau(h)  # back to classical RK4 (still range 2)
+        rk.rk4_chain_set_coupling2(h, 0.0)
+        assert rk.rk4_chain_get_tiling(h)["G"] == 256 * 4 - 8
+    finally:
+        rk.rk4_chain_destroy(h)
