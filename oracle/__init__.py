@@ -75,6 +75,8 @@ def _bind(lib):
     lib.oracle_rk4_integrate.restype = ctypes.c_int
     lib.oracle_rhs.argtypes = [ctypes.c_int, ctypes.c_int, i64, dp, dp, dp]
     lib.oracle_rhs.restype = ctypes.c_int
+    lib.oracle_rk4_integrate_het.argtypes = [ctypes.c_int, ctypes.c_int, i64, dp, ctypes.c_double, i64, dp]
+    lib.oracle_rk4_integrate_het.restype = ctypes.c_int
     lib.oracle_energy_harmonic.argtypes = [ctypes.c_int, i64, dp, dp]
     lib.oracle_energy_harmonic.restype = ctypes.c_double
     lib.oracle_half_norm2.argtypes = [i64, dp]
@@ -110,6 +112,24 @@ def rk4_integrate(y0, model=ROESSLER, bc=PERIODIC, dt=0.01, nsteps=1, prm=None, 
     rc = lib.oracle_rk4_integrate(model, bc, y.shape[0], _dp(prm), float(dt), int(nsteps), _dp(y))
     if rc != 0:
         raise ValueError(f"oracle_rk4_integrate failed: {rc}")
+    return y
+
+
+def site_param_count(model: int) -> int:
+    """Per-site parameters of a heterogeneous chain: Roessler a, b, c, kappa; harmonic omega^2, kappa."""
+    return {ROESSLER: 4, HARMONIC: 2}[model]
+
+
+def rk4_integrate_het(y0, site_params, model=ROESSLER, bc=PERIODIC, dt=0.01, nsteps=1, lib=None) -> np.ndarray:
+    """Classical RK4 on a heterogeneous chain (Eq. (1)): site_params is [N, P]."""
+    lib = lib or load()
+    y = _state(y0, model)
+    sp = np.ascontiguousarray(site_params, dtype=np.float64)
+    if sp.shape != (y.shape[0], site_param_count(model)):
+        raise ValueError("site_params must be [N, P]")
+    rc = lib.oracle_rk4_integrate_het(model, bc, y.shape[0], _dp(sp), float(dt), int(nsteps), _dp(y))
+    if rc != 0:
+        raise ValueError(f"oracle_rk4_integrate_het failed: {rc}")
     return y
 
 

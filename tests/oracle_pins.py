@@ -338,6 +338,95 @@ def pin_nnn_cone(lib, n=96, site=48):
     return ok, f"NNN cone {detail}"
 
 
+# ---- heterogeneous chains, Eq. (1): site-dependent f_i and g_i ---------------------------
+
+def het_params(n, model, seed, kappa_scale=1.0):
+    """Seeded per-site parameters spread around the paper's values."""
+    u = ci.uniform01(seed, 9, 0, 4 * n).reshape(n, 4)
+    if model == ROE:
+        return np.stack([0.15 + 0.1 * u[:, 0], 0.8 + 0.4 * u[:, 1], 8.0 + 2.0 * u[:, 2],
+                         kappa_scale * (0.5 + 1.5 * u[:, 3])], axis=1)
+    return np.stack([0.5 + u[:, 0], kappa_scale * (0.5 + 1.5 * u[:, 1])], axis=1)
+
+
+def pin_het_decoupled(lib, n=7, nsteps=200):
+    """kappa_i = 0: every site is its own oscillator with its own (a_i, b_i, c_i), equal bit for
+    bit to a one-site run of the (pinned) homogeneous integrator with those parameters."""
+    y0 = ci.uniform_state(n, 3, seed=9400)
+    sp = het_params(n, ROE, 9401, kappa_scale=0.0)
+    got = oracle.rk4_integrate_het(y0, sp, ROE, PER, 0.01, nsteps, lib=lib)
+    ok = True
+    for i in range(n):
+        prm = oracle.params(a=sp[i, 0], b=sp[i, 1], c=sp[i, 2], kappa=0.0)
+        one = oracle.rk4_integrate(y0[i:i + 1], ROE, PER, 0.01, nsteps, prm, lib=lib)
+        ok &= bool(np.array_equal(one[0], got[i]))
+    return ok, f"heterogeneous decoupled sites bitwise={ok}"
+
+
+def pin_het_harmonic_eigen(lib, n=40, nsteps=600, dt=0.01, kappa=1.3):
+    """Harmonic chain with site-dependent omega_i and uniform kappa: K = diag(omega_i^2) - kappa L
+    is symmetric, so its eigenvectors (numpy eigh) diagonalise the system and RK4 acts on each
+    eigenmode as R^n (the closed form of the homogeneous chain, per eigenvalue)."""
+    y0 = ci.uniform_state(n, 2, seed=9500)
+    sp = het_params(n, HAR, 9501)
+    sp[:, 1] = kappa
+    worst = 0.0
+    for bc in (PER, FIX):
+        L = -2.0 * np.eye(n) + np.eye(n, k=1) + np.eye(n, k=-1)
+        if bc == PER:
+            L[0, -1] += 1.0
+            L[-1, 0] += 1.0
+        K = np.diag(sp[:, 0]) - kappa * L
+        lam, V = np.linalg.eigh(K)
+        w = np.sqrt(lam)
+        h = w * dt
+        alpha, beta = 1 - h ** 2 / 2 + h ** 4 / 24, 1 - h ** 2 / 6
+        rho, theta = alpha ** 2 + (beta * h) ** 2, np.arctan2(beta * h, alpha)
+        qh, sh = V.T @ y0[:, 0], (V.T @ y0[:, 1]) / w
+        amp, ang = rho ** (nsteps / 2), nsteps * theta
+        q1 = amp * (np.cos(ang) * qh + np.sin(ang) * sh)
+        s1 = amp * (-np.sin(ang) * qh + np.cos(ang) * sh)
+        ref = np.stack([V @ q1, V @ (s1 * w)], axis=1)
+        got = oracle.rk4_integrate_het(y0, sp, HAR, bc, dt, nsteps, lib=lib)
+        worst = max(worst, cf.rel_inf(got, ref))
+    return worst < 1e-12, f"heterogeneous harmonic vs eigen-decomposition rel err {worst:.2e}"
+
+
+def pin_het_roessler_dop853(lib, n=6, T=0.5):
+    """Site-dependent Roessler parameters and couplings: fourth-order convergence to DOP853."""
+    y0 = ci.uniform_state(n, 3, seed=9600)
+    sp = het_params(n, ROE, 9601)
+    worst = []
+    for bc in (PER, FIX):
+        def F(_t, v):
+            r = v.reshape(-1, 3)
+            x, y, z = r[:, 0], r[:, 1], r[:, 2]
+            if bc == PER:
+                xl, xr = np.roll(x, 1), np.roll(x, -1)
+            else:
+                xl, xr = np.concatenate(([0.0], x[:-1])), np.concatenate((x[1:], [0.0]))
+            out = np.empty_like(r)
+            out[:, 0] = -y - z + sp[:, 3] * (xl - 2 * x + xr)
+            out[:, 1] = x + sp[:, 0] * y
+            out[:, 2] = sp[:, 1] + z * (x - sp[:, 2])
+            return out.reshape(-1)
+        ref = solve_ivp(F, (0, T), y0.reshape(-1), method="DOP853", rtol=1e-13, atol=1e-13).y[:, -1].reshape(-1, 3)
+        errs = [cf.rel_inf(oracle.rk4_integrate_het(y0, sp, ROE, bc, dt, int(round(T / dt)), lib=lib), ref)
+                for dt in (0.025, 0.0125)]
+        worst.append(float(np.log2(errs[0] / errs[1])))
+    ok = all(3.8 < p < 4.3 for p in worst)
+    return ok, f"heterogeneous Roessler observed orders {worst}"
+
+
+def pin_het_uniform_equals_homogeneous(lib, n=33, nsteps=100):
+    y0 = ci.uniform_state(n, 3, seed=9700)
+    sp = np.tile([0.2, 1.0, 9.0, 1.3], (n, 1))
+    a = oracle.rk4_integrate_het(y0, sp, ROE, FIX, 0.01, nsteps, lib=lib)
+    b = oracle.rk4_integrate(y0, ROE, FIX, 0.01, nsteps, oracle.params(kappa=1.3), lib=lib)
+    err = cf.rel_inf(a, b)
+    return err < 1e-13, f"uniform heterogeneous vs homogeneous rel err {err:.2e}"
+
+
 ALL_PINS = [
     ("harmonic_modal_per", lambda lib: pin_harmonic_modal(lib, bc=PER)),
     ("harmonic_modal_fix", lambda lib: pin_harmonic_modal(lib, bc=FIX)),
@@ -363,4 +452,8 @@ ALL_PINS = [
     ("nnn_dop853_fix", lambda lib: pin_roessler_vs_dop853(lib, bc=FIX, kappa=1.2, kappa2=0.7)),
     ("nnn_brute_per", lambda lib: pin_brute_force(lib, n=5, model=ROE, bc=PER, kappa2=0.9)),
     ("nnn_brute_fix", lambda lib: pin_brute_force(lib, n=6, model=HAR, bc=FIX, kappa2=0.9)),
+    ("het_decoupled", pin_het_decoupled),
+    ("het_harmonic_eigen", pin_het_harmonic_eigen),
+    ("het_roessler_dop853", pin_het_roessler_dop853),
+    ("het_uniform", pin_het_uniform_equals_homogeneous),
 ]

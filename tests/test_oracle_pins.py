@@ -73,21 +73,35 @@ MUTANTS = [
      "const int64_t first = 0;"),
     ("sign f_y", "ki[1] = x + p->a * y;", "ki[1] = x - p->a * y;"),
     ("transposed f_z", "ki[2] = p->b + z * (x - p->c);", "ki[2] = p->b + x * (z - p->c);"),
-    ("laplacian index", "double lap = xl - 2.0 * x + xr;", "double lap = xl - 2.0 * x + xl;"),
+    ("laplacian index", "double lap = xl - 2.0 * x + xr;   /* Eq. (7)", "double lap = xl - 2.0 * x + xl;   /* Eq. (7)"),
+    ("heterogeneous laplacian index", "double lap = xl - 2.0 * x + xr;\n      ki[0] = -y - z + q[3]",
+     "double lap = xl - 2.0 * x + xl;\n      ki[0] = -y - z + q[3]"),
     ("harmonic omega not squared", "ki[1] = -p->omega0 * p->omega0 * q", "ki[1] = -p->omega0 * q"),
     ("harmonic coupling sign", "q + p->kappa * lap + p->kappa2 * lap2;", "q - p->kappa * lap + p->kappa2 * lap2;"),
     ("periodic wrap", "int64_t il = (i == 0) ? n - 1 : i - 1;", "int64_t il = (i == 0) ? 0 : i - 1;"),
     ("free end instead of fixed", "*xl = (i == 0) ? 0.0 : r[(i - 1) * D];", "*xl = (i == 0) ? r[0] : r[(i - 1) * D];"),
-    ("weights b", "{1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0}", "{1.0 / 6.0, 1.0 / 6.0, 1.0 / 2.0, 1.0 / 6.0}"),
+    ("weights b", "RK4_B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0}",
+     "RK4_B[4] = {1.0 / 6.0, 1.0 / 6.0, 1.0 / 2.0, 1.0 / 6.0}"),
+    ("heterogeneous weights b", "double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0}",
+     "double b[4] = {1.0 / 6.0, 1.0 / 6.0, 1.0 / 2.0, 1.0 / 6.0}"),
+    ("heterogeneous stage coefficient", "double a[4] = {0.0, 0.5, 0.5, 1.0};", "double a[4] = {0.0, 0.5, 1.0, 1.0};"),
     ("a43", "0.0, 0.0, 1.0, 0.0};", "0.0, 0.0, 0.5, 0.0};"),
     ("stage sum truncated", "for (int m = 0; m < j; ++m) sum +=", "for (int m = (j > 0 ? j - 1 : 0); m < j; ++m) sum +="),
     ("stage dt dropped", "sum += A[j * s + m] * dt * k", "sum += A[j * s + m] * k"),
-    ("combine from stage state", "y[e] = y[e] + sum;", "y[e] = r[e] + sum;"),
+    ("combine from stage state", "m < s; ++m) sum += b[m] * dt * k[(int64_t)m * len + e];\n      y[e] = y[e] + sum;",
+     "m < s; ++m) sum += b[m] * dt * k[(int64_t)m * len + e];\n      y[e] = r[e] + sum;"),
+    ("heterogeneous combine from stage state",
+     "m < 4; ++m) sum += b[m] * dt * k[(int64_t)m * len + e];\n      y[e] = y[e] + sum;",
+     "m < 4; ++m) sum += b[m] * dt * k[(int64_t)m * len + e];\n      y[e] = r[e] + sum;"),
     ("stale neighbours", "rhs(model, bc, n, &p, r, k + (int64_t)j * len);",
      "rhs(model, bc, n, &p, (j == s - 1) ? y : r, k + (int64_t)j * len);"),
     ("energy ghost bonds", "for (int64_t i = -1; i < n; ++i) {", "for (int64_t i = 0; i < n - 1; ++i) {"),
     ("energy periodic bond", "y[2 * ((i + 1) % n)] - y[2 * i]", "y[2 * ((i + 2) % n)] - y[2 * i]"),
     ("energy potential", "0.5 * w2 * q * q", "0.5 * q * q"),
+    ("heterogeneous a/b swapped", "ki[1] = x + q[0] * y;", "ki[1] = x + q[1] * y;"),
+    ("heterogeneous neighbour's parameters", "const double *q = sp + 4 * i;", "const double *q = sp + 4 * ((i + 1) % n);"),
+    ("heterogeneous coupling dropped", "ki[0] = -y - z + q[3] * lap;", "ki[0] = -y - z + lap;"),
+    ("heterogeneous harmonic omega", "ki[1] = -q[0] * ri[0] + q[1] * lap;", "ki[1] = -q[1] * ri[0] + q[1] * lap;"),
 ]
 
 
