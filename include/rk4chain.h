@@ -144,6 +144,17 @@ int rk4_chain_set_tableau(rk4_chain *h, int s, const double *A, const double *b)
  * default.  Errors: RK4_EINVAL. */
 int rk4_chain_set_coupling2(rk4_chain *h, double kappa2);
 
+/* Heterogeneous chain (Eq. (1): site-dependent f_i and g_i).  params is a caller-owned device
+ * array of total_sites x P values in the state's precision, 16-byte aligned, kept valid and
+ * unchanged while the handle integrates: RK4_ROESSLER P = 4 (a_i, b_i, c_i, kappa_i),
+ * RK4_HARMONIC P = 2 (omega_i^2, kappa_i); the coupling of site i is
+ * kappa_i (x_{i-1} - 2 x_i + x_{i+1}).  The per-site values replace the handle's (and a
+ * batch's per-chain kappa).  NULL returns to the homogeneous chain.  Supported by the staged
+ * and blocked kernels with the classical tableau (v = 2 or 4 sites per thread); the
+ * persistent and generic kernels return RK4_EUNSUPPORTED, and so does the energy of a
+ * heterogeneous harmonic chain.  Resets the tiling.  Errors: RK4_EINVAL (misaligned). */
+int rk4_chain_set_site_params(rk4_chain *h, const void *params);
+
 /* Times the candidate tilings on the caller's buffers and keeps the fastest (the paper
  * picks G by a performance study, Sec. 3.2.1).  The call integrates `state` (and comp)
  * forward by an unspecified number of steps: pass scratch copies.  Synchronises the stream.

@@ -72,6 +72,7 @@ def _load():
         "rk4_chain_set_time": (c_int, [H, ctypes.c_double]),
         "rk4_chain_set_tableau": (c_int, [H, c_int, dp, dp]),
         "rk4_chain_set_coupling2": (c_int, [H, ctypes.c_double]),
+        "rk4_chain_set_site_params": (c_int, [H, vp]),
         "rk4_chain_destroy": (c_int, [H]),
         "rk4_strerror": (ctypes.c_char_p, [c_int]),
         "rk4_fill_uniform": (c_int, [vp, i64, ctypes.c_uint64, ctypes.c_uint64, c_int, vp]),
@@ -291,6 +292,12 @@ def rk4_chain_set_tableau(h, A=None, b=None):
 
 def rk4_chain_set_coupling2(h, kappa2: float):
     _check(_lib.rk4_chain_set_coupling2(h, float(kappa2)), "rk4_chain_set_coupling2")
+
+
+def rk4_chain_set_site_params(h, params):
+    """Per-site parameters of a heterogeneous chain: a device tensor [total_sites, P] in the
+    state's precision (P = 4 Roessler a, b, c, kappa; P = 2 harmonic omega^2, kappa), or None."""
+    _check(_lib.rk4_chain_set_site_params(h, _ptr(params)), "rk4_chain_set_site_params")
 
 
 def rk4_chain_set_time(h, t0: float):

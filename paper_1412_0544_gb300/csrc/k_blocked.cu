@@ -1,12 +1,13 @@
 // k_blocked.cu -- temporally blocked RK4 kernel: one thread block per (chain, tile) item,
-// k steps per launch (k = 1 is the fused single-step kernel).
+// k steps per launch (k = 1 is the fused single-step kernel).  HET: heterogeneous chains
+// (Eq. (1) of the paper), whose per-site parameters travel with the tile.
 #include <mutex>
 
 #include "rk4_tile.cuh"
 
 namespace rk4d {
 
-template <typename R, int MODEL, int V, bool KAHAN>
+template <typename R, int MODEL, int V, bool KAHAN, bool HET>
 __global__ void __launch_bounds__(max_threads_for(V)) k_blocked(BlockedJob job, Coef<R> cf) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t item = blockIdx.x;
@@ -21,46 +22,54 @@ __global__ void __launch_bounds__(max_threads_for(V)) k_blocked(BlockedJob job, 
     tile = item - job.tile_prefix[ci];
     c.kappa = (R)ch.kappa;
   }
-  tile_item<R, MODEL, V, KAHAN, false>(static_cast<const R *>(job.in), static_cast<R *>(job.out),
-                                static_cast<const R *>(job.cin), static_cast<R *>(job.cout), ch, tile, job.K,
-                                job.G, c, smem);
+  tile_item<R, MODEL, V, KAHAN, false, HET>(static_cast<const R *>(job.in), static_cast<R *>(job.out),
+                                            static_cast<const R *>(job.cin), static_cast<R *>(job.cout), ch, tile,
+                                            job.K, job.G, c, smem, static_cast<const R *>(job.sp));
 }
 
-size_t blocked_smem_bytes(int model, bool fp32, int v, int block) {
+size_t blocked_smem_bytes(int model, bool fp32, int v, int block, bool het) {
   const int D = model == ROESSLER ? 3 : 2;
+  const int P = model == ROESSLER ? 4 : 2;
   const size_t rs = fp32 ? 4 : 8;
-  return 128 * rs + (size_t)block * v * D * rs * (fp32 ? 2 : 1);
+  return 128 * rs + (size_t)block * v * rs * (D * (fp32 ? 2 : 1) + (het ? P : 0));
 }
 
-template <typename R, int MODEL, int V, bool KAHAN>
+template <typename R, int MODEL, int V, bool KAHAN, bool HET>
 static cudaError_t launch_one(int block, const BlockedJob &job, const CoefD &cfd, cudaStream_t st) {
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_blocked<R, MODEL, V, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr_err = cudaFuncSetAttribute(k_blocked<R, MODEL, V, KAHAN, HET>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     200 * 1024);
   });
   if (attr_err != cudaSuccess) return attr_err;
-  const size_t smem = blocked_smem_bytes(MODEL, KAHAN, V, block);
+  const size_t smem = blocked_smem_bytes(MODEL, KAHAN, V, block, HET);
   Coef<R> cf = to_coef<R>(cfd, cfd.kappa);
   if (job.ntiles <= 0) return cudaSuccess;
-  k_blocked<R, MODEL, V, KAHAN><<<(unsigned)job.ntiles, block, smem, st>>>(job, cf);
+  k_blocked<R, MODEL, V, KAHAN, HET><<<(unsigned)job.ntiles, block, smem, st>>>(job, cf);
   return cudaGetLastError();
 }
 
-template <int MODEL, int V>
+template <int MODEL, int V, bool HET>
 static cudaError_t launch_v(bool fp32, int block, const BlockedJob &job, const CoefD &cf, cudaStream_t st) {
-  return fp32 ? launch_one<float, MODEL, V, true>(block, job, cf, st)
-              : launch_one<double, MODEL, V, false>(block, job, cf, st);
+  return fp32 ? launch_one<float, MODEL, V, true, HET>(block, job, cf, st)
+              : launch_one<double, MODEL, V, false, HET>(block, job, cf, st);
 }
 
 template <int MODEL>
 static cudaError_t launch_m(bool fp32, int v, int block, const BlockedJob &job, const CoefD &cf, cudaStream_t st) {
+  if (job.sp) {  // heterogeneous chains: 2 or 4 sites per thread
+    switch (v) {
+      case 2: return launch_v<MODEL, 2, true>(fp32, block, job, cf, st);
+      case 4: return launch_v<MODEL, 4, true>(fp32, block, job, cf, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (v) {
-    case 1: return launch_v<MODEL, 1>(fp32, block, job, cf, st);
-    case 2: return launch_v<MODEL, 2>(fp32, block, job, cf, st);
-    case 4: return launch_v<MODEL, 4>(fp32, block, job, cf, st);
-    case 8: return launch_v<MODEL, 8>(fp32, block, job, cf, st);
+    case 1: return launch_v<MODEL, 1, false>(fp32, block, job, cf, st);
+    case 2: return launch_v<MODEL, 2, false>(fp32, block, job, cf, st);
+    case 4: return launch_v<MODEL, 4, false>(fp32, block, job, cf, st);
+    case 8: return launch_v<MODEL, 8, false>(fp32, block, job, cf, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -71,26 +80,36 @@ cudaError_t launch_blocked(int model, bool fp32, int v, int block, const Blocked
                            : launch_m<HARMONIC>(fp32, v, block, job, cf, st);
 }
 
-template <typename R, int MODEL, int V, bool KAHAN>
+template <typename R, int MODEL, int V, bool KAHAN, bool HET>
 static int max_threads_one() {
   cudaFuncAttributes a;
-  if (cudaFuncGetAttributes(&a, k_blocked<R, MODEL, V, KAHAN>) != cudaSuccess) return 0;
+  if (cudaFuncGetAttributes(&a, k_blocked<R, MODEL, V, KAHAN, HET>) != cudaSuccess) return 0;
   return a.maxThreadsPerBlock;
 }
 
+template <int MODEL, int V, bool HET>
+static int max_threads_v(bool fp32) {
+  return fp32 ? max_threads_one<float, MODEL, V, true, HET>() : max_threads_one<double, MODEL, V, false, HET>();
+}
+
 template <int MODEL>
-static int max_threads_m(bool fp32, int v) {
+static int max_threads_m(bool fp32, int v, bool het) {
+  if (het) {
+    if (v == 2) return max_threads_v<MODEL, 2, true>(fp32);
+    if (v == 4) return max_threads_v<MODEL, 4, true>(fp32);
+    return 0;
+  }
   switch (v) {
-    case 1: return fp32 ? max_threads_one<float, MODEL, 1, true>() : max_threads_one<double, MODEL, 1, false>();
-    case 2: return fp32 ? max_threads_one<float, MODEL, 2, true>() : max_threads_one<double, MODEL, 2, false>();
-    case 4: return fp32 ? max_threads_one<float, MODEL, 4, true>() : max_threads_one<double, MODEL, 4, false>();
-    case 8: return fp32 ? max_threads_one<float, MODEL, 8, true>() : max_threads_one<double, MODEL, 8, false>();
+    case 1: return max_threads_v<MODEL, 1, false>(fp32);
+    case 2: return max_threads_v<MODEL, 2, false>(fp32);
+    case 4: return max_threads_v<MODEL, 4, false>(fp32);
+    case 8: return max_threads_v<MODEL, 8, false>(fp32);
     default: return 0;
   }
 }
 
-int blocked_max_threads(int model, bool fp32, int v) {
-  return model == ROESSLER ? max_threads_m<ROESSLER>(fp32, v) : max_threads_m<HARMONIC>(fp32, v);
+int blocked_max_threads(int model, bool fp32, int v, bool het) {
+  return model == ROESSLER ? max_threads_m<ROESSLER>(fp32, v, het) : max_threads_m<HARMONIC>(fp32, v, het);
 }
 
 }  // namespace rk4d

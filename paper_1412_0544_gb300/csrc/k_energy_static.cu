@@ -61,8 +61,10 @@ extern "C" int rk4_chain_energy_static(rk4_chain *h, const void *state, const vo
   const ChainDesc *chains = nullptr;
   CoefD cf{};
   cudaStream_t st = nullptr;
+  bool het = false;
   if (!out || !state) return RK4_EINVAL;
-  if (handle_info(h, &model, &fp32, &nchains, &chains, &cf, &st) != RK4_OK) return RK4_EINVAL;
+  if (handle_info(h, &model, &fp32, &nchains, &chains, &cf, &st, &het) != RK4_OK) return RK4_EINVAL;
+  if (het && model == RK4_HARMONIC) return RK4_EUNSUPPORTED;  // as rk4_chain_energy
   if (fp32 != (comp != nullptr)) return RK4_EINVAL;
   if (nchains < 1 || nchains > kStaticMaxChains) return RK4_EINVAL;
   StaticScratch *s = nullptr;

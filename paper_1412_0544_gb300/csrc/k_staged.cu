@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(256) k_staged(StagedJob job, Coef<R> cf, int j
       ch = job.chains[lo];
       c.kappa = (R)ch.kappa;
     }
+    if (job.sp) c = site_coef<R, MODEL>(c, static_cast<const R *>(job.sp) + i * Dim<MODEL>::P);  // Eq. (1)
     const int64_t li = i - ch.off;  // index within the chain
     R u[D], y[D], acc[D], cmp[D], k[D];
 #pragma unroll

@@ -27,9 +27,11 @@ struct GraphKey {
   int64_t nsteps = -1;
   int block = 0, v = 0, k = 0;
   long long timeout = 0;
+  const void *sp = nullptr;
+  int generic = 0;
   bool operator==(const GraphKey &o) const {
     return kernel == o.kernel && state == o.state && comp == o.comp && ws == o.ws && nsteps == o.nsteps &&
-           block == o.block && v == o.v && k == o.k && timeout == o.timeout;
+           block == o.block && v == o.v && k == o.k && timeout == o.timeout && sp == o.sp && generic == o.generic;
   }
 };
 
@@ -81,6 +83,9 @@ struct rk4_chain {
   bool has_tableau = false;
   TableauD tab{};
   double kappa2 = 0.0;
+  // heterogeneous chain (Eq. (1)): caller-owned device array of P parameters per site
+  const void *site_params = nullptr;
+  unsigned gen_version = 0;  // bumped when the tableau or kappa2 changes (graph cache key)
 };
 
 namespace {
@@ -96,6 +101,7 @@ size_t elem_bytes(const rk4_chain *h) { return h->fp32 ? 4 : 8; }
 
 // The generic kernels run when a tableau was set or second-neighbour coupling is on.
 bool use_generic(const rk4_chain *h) { return h->has_tableau || h->kappa2 != 0.0; }
+bool use_het(const rk4_chain *h) { return h->site_params != nullptr; }
 int coupling_range(const rk4_chain *h) { return h->kappa2 != 0.0 ? 2 : 1; }
 int stages(const rk4_chain *h) { return use_generic(h) ? h->tab.s : 4; }
 
@@ -171,14 +177,15 @@ int tiling_valid(const rk4_chain *h, int block, int v, int k) {
     return 1;
   }
   if (v != 1 && v != 2 && v != 4 && v != 8) return 0;
+  if (use_het(h) && v != 2 && v != 4) return 0;
   if (W - 8 * k < 8 * k) return 0;
-  if (blocked_smem_bytes(h->model, h->fp32, v, block) > kMaxSmem) return 0;
+  if (blocked_smem_bytes(h->model, h->fp32, v, block, use_het(h)) > kMaxSmem) return 0;
   return 1;
 }
 
 int tiling_max_threads(const rk4_chain *h, int v) {
   return use_generic(h) ? gen_blocked_max_threads(h->model, h->fp32, coupling_range(h), v)
-                        : blocked_max_threads(h->model, h->fp32, v);
+                        : blocked_max_threads(h->model, h->fp32, v, use_het(h));
 }
 
 void default_tiling(rk4_chain *h) {
@@ -190,6 +197,10 @@ void default_tiling(rk4_chain *h) {
     h->tiling.block = 128;
     h->tiling.v = 2;
     h->tiling.k = 1;
+  } else if (use_het(h)) {
+    h->tiling.block = 256;
+    h->tiling.v = 2;
+    h->tiling.k = h->fp32 ? 4 : 1;
   } else {
     h->tiling.block = 256;
     h->tiling.v = 4;
@@ -321,6 +332,7 @@ cudaError_t enqueue_integrate(rk4_chain *h, int kernel, void *state, void *comp,
     StagedJob j{};
     j.y = state;
     j.cmp = comp;
+    j.sp = h->site_params;
     j.nchains = h->nchains;
     j.one = h->chains[0];
     j.chains = dev_chains(h, ws, L);
@@ -345,6 +357,7 @@ cudaError_t enqueue_integrate(rk4_chain *h, int kernel, void *state, void *comp,
     j.nchains = h->nchains;
     j.one = h->chains[0];
     j.chains = dev_chains(h, ws, L);
+    j.sp = h->site_params;
     const int32_t *pre = h->nchains > 1 ? reinterpret_cast<const int32_t *>(ws + L.prefix) : nullptr;
     for (int64_t i = 0; i < P.count(); ++i) {
       const int k = P.k_at(i);
@@ -418,7 +431,8 @@ int integrate_impl(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_by
   if (rc) return rc;
   if (nsteps < 0) return RK4_EINVAL;
   const int kernel = effective_kernel(h);
-  if (kernel == RK4_KERNEL_PERSISTENT && use_generic(h)) return RK4_EUNSUPPORTED;
+  if (kernel == RK4_KERNEL_PERSISTENT && (use_generic(h) || use_het(h))) return RK4_EUNSUPPORTED;
+  if (use_generic(h) && use_het(h)) return RK4_EUNSUPPORTED;
   const WsLayout L = layout(h, kernel);
   if (ws_bytes < L.total) return RK4_ENOMEM_WS;
   if (nsteps == 0) return RK4_OK;
@@ -448,6 +462,8 @@ int integrate_impl(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_by
   key.v = h->tiling.v;
   key.k = h->tiling.k;
   key.timeout = h->timeout_ns;
+  key.sp = h->site_params;
+  key.generic = use_generic(h) ? 1 + (int)h->gen_version : 0;
   if (!(h->gexec && key == h->gkey)) {
     if (h->gexec) {
       cudaGraphExecDestroy(h->gexec);
@@ -503,8 +519,9 @@ rk4_chain *new_handle(int model, int precision, double dt, const rk4_params *p, 
 
 // Read-only view of a handle for the allocation-free reduction entry point.
 int rk4d::handle_info(const rk4_chain *h, int *model, bool *fp32, int *nchains, const ChainDesc **chains, CoefD *cf,
-                      cudaStream_t *stream) {
+                      cudaStream_t *stream, bool *het) {
   if (!h) return RK4_EINVAL;
+  *het = use_het(h);
   *model = h->model;
   *fp32 = h->fp32;
   *nchains = h->nchains;
@@ -657,6 +674,7 @@ int rk4_chain_integrate_host(rk4_chain *h, void *host_state, void *host_comp, vo
 
 int rk4_chain_energy(rk4_chain *h, const void *state, const void *comp, void *ws, size_t ws_bytes, double *out) {
   if (!h || !out) return RK4_EINVAL;
+  if (use_het(h) && h->model == RK4_HARMONIC) return RK4_EUNSUPPORTED;
   int rc = check_buffers(h, state, comp, ws);
   if (rc) return rc;
   const WsLayout L = layout(h, effective_kernel(h));
@@ -843,6 +861,7 @@ int rk4_chain_set_tableau(rk4_chain *h, int s, const double *A, const double *b)
   }
   h->has_tableau = true;
   h->tab = t;
+  h->gen_version++;
   default_tiling(h);
   return RK4_OK;
 }
@@ -851,6 +870,15 @@ int rk4_chain_set_coupling2(rk4_chain *h, double kappa2) {
   if (!h || !std::isfinite(kappa2)) return RK4_EINVAL;
   h->kappa2 = kappa2;
   if (!h->has_tableau) h->tab = classical_rk4();
+  h->gen_version++;
+  default_tiling(h);
+  return RK4_OK;
+}
+
+int rk4_chain_set_site_params(rk4_chain *h, const void *params) {
+  if (!h) return RK4_EINVAL;
+  if (params && (reinterpret_cast<uintptr_t>(params) % 16) != 0) return RK4_EINVAL;
+  h->site_params = params;
   default_tiling(h);
   return RK4_OK;
 }

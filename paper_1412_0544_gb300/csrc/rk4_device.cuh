@@ -28,8 +28,10 @@ enum { ROESSLER = 0, HARMONIC = 1 };
 enum { PERIODIC = 0, FIXED = 1 };
 
 template <int MODEL> struct Dim;
-template <> struct Dim<ROESSLER> { static constexpr int D = 3; };
-template <> struct Dim<HARMONIC> { static constexpr int D = 2; };
+template <> struct Dim<ROESSLER> { static constexpr int D = 3; static constexpr int P = 4; };
+template <> struct Dim<HARMONIC> { static constexpr int D = 2; static constexpr int P = 2; };
+// P: parameters per site of a heterogeneous chain (Eq. (1) of the paper): Roessler a, b, c,
+// kappa; harmonic omega^2, kappa.
 
 __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
@@ -89,6 +91,23 @@ __device__ __forceinline__ void stage_update(int j, const R *k, R *y, R *u, R *a
       }
     }
   }
+}
+
+// Coefficients of one site of a heterogeneous chain: the chain's coefficients with the
+// site's own parameters p[0..P-1] substituted.
+template <typename R, int MODEL>
+__device__ __forceinline__ Coef<R> site_coef(const Coef<R> &cf, const R *p) {
+  Coef<R> c = cf;
+  if constexpr (MODEL == ROESSLER) {
+    c.a = p[0];
+    c.b = p[1];
+    c.c = p[2];
+    c.kappa = p[3];
+  } else {
+    c.w2 = p[0];
+    c.kappa = p[1];
+  }
+  return c;
 }
 
 // Positive modulus for periodic index wrapping.

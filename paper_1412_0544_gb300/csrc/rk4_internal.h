@@ -55,6 +55,7 @@ struct BlockedJob {
   int K;                        // steps in this launch
   int G;                        // interior sites per tile
   int64_t ntiles;               // tiles in the launch
+  const void *sp;               // per-site parameters of a heterogeneous chain, or NULL
 };
 
 struct StagedJob {
@@ -67,6 +68,7 @@ struct StagedJob {
   ChainDesc one;
   const ChainDesc *chains;   // device table for batches (site -> chain by binary search)
   int64_t total;             // total sites
+  const void *sp;            // per-site parameters of a heterogeneous chain, or NULL
 };
 
 // One step of the generic standard scheme: stage states, slopes and the combination, each a
@@ -103,7 +105,7 @@ struct PersistentJob {
 
 // Launchers (return a cudaError_t).  R is selected by `fp32` (FP32 + Kahan) or double.
 cudaError_t launch_blocked(int model, bool fp32, int v, int block, const BlockedJob &job, const CoefD &cf,
-                           cudaStream_t st);
+                           cudaStream_t st);  // job.sp != NULL selects the heterogeneous kernel (v = 2 or 4)
 cudaError_t launch_staged(int model, bool fp32, int stage, const StagedJob &job, const CoefD &cf,
                           cudaStream_t st);
 cudaError_t launch_persistent(int model, bool fp32, int v, int block, int grid, const PersistentJob &job,
@@ -120,8 +122,8 @@ cudaError_t launch_gen_blocked(int model, bool fp32, int range, int v, int block
                                const CoefD &cf, const TableauD &tb, double dt, int H, cudaStream_t st);
 size_t gen_blocked_smem_bytes(int model, bool fp32, int v, int block);
 int gen_blocked_max_threads(int model, bool fp32, int range, int v);
-size_t blocked_smem_bytes(int model, bool fp32, int v, int block);
-int blocked_max_threads(int model, bool fp32, int v);
+size_t blocked_smem_bytes(int model, bool fp32, int v, int block, bool het = false);
+int blocked_max_threads(int model, bool fp32, int v, bool het = false);
 
 constexpr int kEnergyBlocks = 1024;  // fixed grid of the single-chain reduction (deterministic)
 
@@ -131,6 +133,6 @@ struct rk4_chain;
 namespace rk4d {
 // Read-only view of a handle (model, precision, chain table on the host, coefficients, stream).
 int handle_info(const rk4_chain *h, int *model, bool *fp32, int *nchains, const ChainDesc **chains, CoefD *cf,
-                cudaStream_t *stream);
+                cudaStream_t *stream, bool *het);
 
 }  // namespace rk4d

@@ -44,9 +44,10 @@ __device__ __forceinline__ void st_shared_if(bool p, double *a, double v) {
 // Stage 0 of every step reads y directly (it is the stage state), so no register copies are
 // needed between steps.  The warp-edge exchange is branch-free: predicated stores by lanes 0
 // and 31, uniform (broadcast) loads by every lane, and selects.
-template <typename R, int MODEL, int V, bool KAHAN, bool MASK>
+template <typename R, int MODEL, int V, bool KAHAN, bool MASK, bool HET = false>
 __device__ __forceinline__ void tile_advance(R (&y)[V][Dim<MODEL>::D], R (&cmp)[V][Dim<MODEL>::D],
-                                             uint32_t ghost, int K, const Coef<R> &cf, R *edge) {
+                                             uint32_t ghost, int K, const Coef<R> &cf, R *edge,
+                                             const Coef<R> *cs = nullptr) {
   constexpr int D = Dim<MODEL>::D;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -81,7 +82,10 @@ __device__ __forceinline__ void tile_advance(R (&y)[V][Dim<MODEL>::D], R (&cmp)[
         const R xl = (v == 0) ? left : xs[v - 1];
         const R xr = (v == V - 1) ? right : xs[v + 1];
         R k[D];
-        slope<R, MODEL>((j == 0) ? y[v] : u[v], xl, xr, cf, k);
+        if constexpr (HET)
+          slope<R, MODEL>((j == 0) ? y[v] : u[v], xl, xr, cs[v], k);  // site-dependent f_i, g_i (Eq. (1))
+        else
+          slope<R, MODEL>((j == 0) ? y[v] : u[v], xl, xr, cf, k);
         stage_update<R, D, KAHAN>(j, k, y[v], u[v], acc[v], cmp[v], cf);
       }
     }
@@ -146,21 +150,24 @@ __device__ __forceinline__ void tile_store(R *__restrict__ dst, const R *tile, i
 }
 
 // Process one (chain, tile) item end to end: load, advance K steps, store the interior.
-// Shared memory: edge[128] | tile[W*D] | ctile[W*D] (Kahan).
-template <typename R, int MODEL, int V, bool KAHAN, bool COH>
+// Shared memory: edge[128] | tile[W*D] | ctile[W*D] (Kahan) | ptile[W*P] (heterogeneous).
+template <typename R, int MODEL, int V, bool KAHAN, bool COH, bool HET = false>
 __device__ __forceinline__ void tile_item(const R *__restrict__ in, R *__restrict__ out, const R *__restrict__ cin,
                                           R *__restrict__ cout, const ChainDesc &ch, int64_t tile, int K, int G,
-                                          const Coef<R> &cf, unsigned char *smem) {
+                                          const Coef<R> &cf, unsigned char *smem, const R *__restrict__ sp = nullptr) {
   constexpr int D = Dim<MODEL>::D;
+  constexpr int P = Dim<MODEL>::P;
   R *edge = reinterpret_cast<R *>(smem);
   R *tl = edge + 128;
   const int W = blockDim.x * V;
   R *ctl = tl + W * D;
+  R *ptl = ctl + (KAHAN ? W * D : 0);
   const int H = 4 * K;
   const int64_t t0 = tile * (int64_t)G - H;
 
   tile_load<R, D, COH>(tl, in, ch.off, ch.n, ch.bc, t0, W);
   if constexpr (KAHAN) tile_load<R, D, COH>(ctl, cin, ch.off, ch.n, ch.bc, t0, W);
+  if constexpr (HET) tile_load<R, P, COH>(ptl, sp, ch.off, ch.n, ch.bc, t0, W);
   __syncthreads();
 
   R y[V][D], cmp[V][D];
@@ -173,6 +180,12 @@ __device__ __forceinline__ void tile_item(const R *__restrict__ in, R *__restric
       if constexpr (KAHAN) cmp[v][d] = ctl[(base + v) * D + d]; else cmp[v][d] = R(0);
     }
 
+  Coef<R> cs[HET ? V : 1];
+  if constexpr (HET) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) cs[v] = site_coef<R, MODEL>(cf, ptl + (base + v) * P);
+  }
+
   const bool edge_tile = (ch.bc == FIXED) && (t0 < 0 || t0 + W > ch.n);
   if (edge_tile) {
     uint32_t ghost = 0;
@@ -181,9 +194,9 @@ __device__ __forceinline__ void tile_item(const R *__restrict__ in, R *__restric
       const int64_t g = t0 + base + v;
       if (g < 0 || g >= ch.n) ghost |= 1u << v;
     }
-    tile_advance<R, MODEL, V, KAHAN, true>(y, cmp, ghost, K, cf, edge);
+    tile_advance<R, MODEL, V, KAHAN, true, HET>(y, cmp, ghost, K, cf, edge, cs);
   } else {
-    tile_advance<R, MODEL, V, KAHAN, false>(y, cmp, 0u, K, cf, edge);
+    tile_advance<R, MODEL, V, KAHAN, false, HET>(y, cmp, 0u, K, cf, edge, cs);
   }
 
 #pragma unroll

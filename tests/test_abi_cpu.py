@@ -181,3 +181,18 @@ def test_generic_scheme_validation(rk):
         assert rk.rk4_chain_get_tiling(h)["G"] == 256 * 4 - 8
     finally:
         rk.rk4_chain_destroy(h)
+
+
+def test_site_params_validation(rk):
+    h = rk.rk4_chain_create(0, 0, 1000, 0.01, 0)
+    try:
+        with pytest.raises(rk.RK4Error):  # device pointers must be 16-byte aligned
+            rk.rk4_chain_set_site_params(h, 4096 + 8)
+        rk.rk4_chain_set_site_params(h, 4096)
+        assert rk.rk4_chain_get_tiling(h)["v"] in (2, 4)
+        with pytest.raises(rk.RK4Error):  # heterogeneous kernels have 2 or 4 sites per thread
+            rk.rk4_chain_set_tiling(h, 128, 8, 1)
+        rk.rk4_chain_set_site_params(h, None)
+        rk.rk4_chain_set_tiling(h, 128, 8, 1)
+    finally:
+        rk.rk4_chain_destroy(h)
