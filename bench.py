@@ -50,7 +50,8 @@ FP32K_INST_PER_SITE_STEP = 61    # + 4 per component for the Kahan update
 # DRAM traffic (read + write bytes) per launch of the FP64 blocked kernel at N = 2^24 from one
 # ncu --set full capture, valid only for the kernel sources (hash) and the tiling recorded with
 # it; any other combination reports null.
-TRAFFIC = {("497dae5f7adf461d", "256,4,2"): 402940416 + 357950208}
+TRAFFIC = {("d92f26e96980e065", "256,4,1"): 402767360 + 357237760,
+           ("d92f26e96980e065", "256,4,2"): 402888448 + 356931584}
 
 
 def kernel_hash() -> str:
@@ -332,6 +333,63 @@ def size_sweep(args):
     return 0
 
 
+# Dormand and Prince (1980) RK5(4)7M, fifth-order weights, used with a fixed step
+DOPRI5_A = np.array([
+    [0, 0, 0, 0, 0, 0, 0],
+    [1 / 5, 0, 0, 0, 0, 0, 0],
+    [3 / 40, 9 / 40, 0, 0, 0, 0, 0],
+    [44 / 45, -56 / 15, 32 / 9, 0, 0, 0, 0],
+    [19372 / 6561, -25360 / 2187, 64448 / 6561, -212 / 729, 0, 0, 0],
+    [9017 / 3168, -355 / 33, 46732 / 5247, 49 / 176, -5103 / 18656, 0, 0],
+    [35 / 384, 0, 500 / 1113, 125 / 192, -2187 / 6784, 11 / 84, 0]])
+DOPRI5_B = np.array([35 / 384, 0, 500 / 1113, 125 / 192, -2187 / 6784, 11 / 84, 0])
+
+
+def generic_fp_ops(A, b, D, slope_ops, kahan):
+    """Floating-point instructions per site-step of the generic kernel: stage-state FMAs, slopes,
+    weighted sum, update (FP32-Kahan: 4 per component instead of 1)."""
+    s = len(b)
+    return (int(np.count_nonzero(np.tril(A, -1))) * D + s * slope_ops + int(np.count_nonzero(b)) * D
+            + (4 if kahan else 1) * D)
+
+
+def variant_extra(rk, torch, stream, precision, *, generic=False, het=False, n=N_SITES, nsteps=200):
+    """The widened scheme on the same N = 2^24 periodic Roessler chain: Dormand-Prince 5 with
+    second-neighbour coupling (generic kernel, halo 14 sites per side per step), or a
+    heterogeneous chain with per-site parameters (Eq. (1))."""
+    import chain_inputs as ci
+    fp32 = precision == rk.RK4_FP32_KAHAN
+    dtype = torch.float32 if fp32 else torch.float64
+    h = rk.rk4_chain_create(rk.RK4_ROESSLER, precision, n, DT, rk.RK4_PERIODIC, None, stream)
+    try:
+        sp = None
+        if generic:
+            rk.rk4_chain_set_tableau(h, DOPRI5_A, DOPRI5_B)
+            rk.rk4_chain_set_coupling2(h, 0.5)
+            ops = generic_fp_ops(DOPRI5_A, DOPRI5_B, D, 10, fp32)
+        if het:
+            u = ci.uniform01(SEED, 9, 0, 4 * n).reshape(n, 4)
+            sp = torch.from_numpy(np.stack([0.15 + 0.1 * u[:, 0], 0.8 + 0.4 * u[:, 1], 8.0 + 2.0 * u[:, 2],
+                                            0.5 + 1.5 * u[:, 3]], axis=1)).to(dtype).cuda()
+            rk.rk4_chain_set_site_params(h, sp)
+            ops = FP32K_INST_PER_SITE_STEP if fp32 else FP64_INST_PER_SITE_STEP
+        st = torch.empty((n, D), dtype=dtype, device="cuda")
+        rk.rk4_fill_uniform(st, n * D, SEED, 0, precision, stream)
+        cp = torch.zeros_like(st) if fp32 else None
+        ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+        best = rk.rk4_chain_autotune(h, st.clone(), cp.clone() if cp is not None else None, ws, 16)
+        rk.rk4_chain_integrate(h, st, cp, ws, 2 * best["k"])
+        el = time_integrate(rk, h, st, cp, ws, nsteps, 1, torch)
+        sps = n * nsteps / el
+        peak = FP32_INST_PEAK if fp32 else FP64_INST_PEAK
+        return {"value": sps, "unit": "site-steps/s", "N": n, "steps": nsteps, "tiling": best,
+                "fp_inst_per_site_step": ops, "pipe_frac_of_measured": sps * ops / peak,
+                "scheme": ("Dormand-Prince 5 (7 stages) + second-neighbour coupling" if generic
+                           else "heterogeneous chain, per-site a, b, c, kappa")}
+    finally:
+        rk.rk4_chain_destroy(h)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -436,6 +494,12 @@ def main():
         extras["fp32_kahan_2e27"] = fp32_kahan_extra(rk, torch, stream)
         extras["batch_fp64"] = batch_extra(rk, torch, stream, rk.RK4_FP64)
         extras["batch_fp32_kahan"] = batch_extra(rk, torch, stream, rk.RK4_FP32_KAHAN)
+        extras["generic_dopri5_nnn_fp64"] = variant_extra(rk, torch, stream, rk.RK4_FP64, generic=True)
+        extras["generic_dopri5_nnn_fp32_kahan"] = variant_extra(rk, torch, stream, rk.RK4_FP32_KAHAN, generic=True,
+                                                                nsteps=1000)
+        extras["heterogeneous_fp64"] = variant_extra(rk, torch, stream, rk.RK4_FP64, het=True)
+        extras["heterogeneous_fp32_kahan"] = variant_extra(rk, torch, stream, rk.RK4_FP32_KAHAN, het=True,
+                                                           nsteps=1000)
     rk.rk4_chain_destroy(h)
 
     out = None

@@ -8,7 +8,7 @@ namespace rk4d {
 
 // Largest block of the generic tile kernel by sites per thread (it keeps every stage slope
 // of every site in registers).
-__host__ __device__ constexpr int gen_max_threads(int v) { return v <= 2 ? 256 : 128; }
+__host__ __device__ constexpr int gen_max_threads(int v) { return v <= 4 ? 256 : 128; }
 
 // The tableau in the working precision: a_jm dt and b_m dt rounded once on the host, plus
 // bit masks of the nonzero entries (zero entries are skipped, in every kernel alike).
