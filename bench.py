@@ -273,11 +273,23 @@ def batch_extra(rk, torch, stream, precision, nsteps=NSTEPS):
         rk.rk4_fill_uniform(st, total * D, SEED, 0, precision, stream)
         cp = torch.zeros_like(st) if precision == rk.RK4_FP32_KAHAN else None
         ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
-        best = rk.rk4_chain_autotune(h, st.clone(), cp.clone() if cp is not None else None, ws, 32)
+        out = {"unit": "site-steps/s", "chains": 4096, "sites": total, "steps": nsteps}
+        # the persistent scheme (one cooperative launch, CUDA graph), then the autotuner's choice
+        rk.rk4_chain_set_kernel(h, rk.RK4_KERNEL_PERSISTENT)
+        tp = rk.rk4_chain_autotune(h, st.clone(), cp.clone() if cp is not None else None, ws, 32)
         rk.rk4_chain_integrate(h, st, cp, ws, nsteps)  # capture + warm-up
         el = time_integrate(rk, h, st, cp, ws, nsteps, 1, torch)
-        return {"value": total * nsteps / el, "unit": "site-steps/s", "chains": 4096, "sites": total,
-                "steps": nsteps, "tiling": best, "kernel": "persistent cooperative, CUDA graph"}
+        out["persistent"] = {"value": total * nsteps / el, "tiling": tp,
+                             "kernel": "persistent cooperative, one launch per call, CUDA graph"}
+        rk.rk4_chain_set_kernel(h, rk.RK4_KERNEL_AUTO)
+        best = rk.rk4_chain_autotune(h, st.clone(), cp.clone() if cp is not None else None, ws, 32)
+        kern = rk.rk4_chain_get_kernel(h)
+        rk.rk4_chain_integrate(h, st, cp, ws, nsteps)
+        el = time_integrate(rk, h, st, cp, ws, nsteps, 1, torch)
+        out.update({"value": total * nsteps / el, "tiling": best,
+                    "kernel": ("persistent cooperative" if kern == rk.RK4_KERNEL_PERSISTENT
+                               else "blocked, one launch per k steps") + ", CUDA graph (autotuned)"})
+        return out
     finally:
         rk.rk4_chain_destroy(h)
 

@@ -118,9 +118,13 @@ int rk4_chain_workspace_bytes(const rk4_chain *h, size_t *bytes);
 /* Total sites (sum over chains) and per-site dimension D of the handle's state. */
 int rk4_chain_shape(const rk4_chain *h, int64_t *total_sites, int *dim);
 
-/* Chooses the scheme (enum rk4_kernel).  AUTO picks BLOCKED for one chain and PERSISTENT
- * for a batch.  Errors: RK4_EINVAL. */
+/* Chooses the scheme (enum rk4_kernel).  AUTO picks BLOCKED for one chain (and for the
+ * generic and heterogeneous schemes) and, for a batch, PERSISTENT -- or BLOCKED if
+ * rk4_chain_autotune measured it faster.  Errors: RK4_EINVAL. */
 int rk4_chain_set_kernel(rk4_chain *h, int kernel);
+
+/* The scheme the handle will run (AUTO resolved).  Errors: RK4_EINVAL. */
+int rk4_chain_get_kernel(const rk4_chain *h, int *kernel);
 
 /* Sets the tiling (block, v, k; G is computed).  block = 0 restores the automatic choice.
  * Errors: RK4_EINVAL when block, v or k is out of range or G < 8k. */
@@ -156,7 +160,8 @@ int rk4_chain_set_coupling2(rk4_chain *h, double kappa2);
 int rk4_chain_set_site_params(rk4_chain *h, const void *params);
 
 /* Times the candidate tilings on the caller's buffers and keeps the fastest (the paper
- * picks G by a performance study, Sec. 3.2.1).  The call integrates `state` (and comp)
+ * picks G by a performance study, Sec. 3.2.1); for a batch on RK4_KERNEL_AUTO it also times
+ * the persistent against the blocked scheme and keeps the faster.  The call integrates `state` (and comp)
  * forward by an unspecified number of steps: pass scratch copies.  Synchronises the stream.
  * *best (may be NULL) receives the chosen tiling.  Errors: RK4_EINVAL, RK4_ENOMEM_WS,
  * RK4_ECUDA. */

@@ -60,6 +60,7 @@ def _load():
         "rk4_chain_set_kernel": (c_int, [H, c_int]),
         "rk4_chain_set_tiling": (c_int, [H, c_int, c_int, c_int]),
         "rk4_chain_get_tiling": (c_int, [H, ctypes.POINTER(rk4_tiling)]),
+        "rk4_chain_get_kernel": (c_int, [H, ctypes.POINTER(c_int)]),
         "rk4_chain_autotune": (c_int, [H, vp, vp, vp, sz, c_int, ctypes.POINTER(rk4_tiling)]),
         "rk4_chain_step": (c_int, [H, vp, vp, vp, sz, dp]),
         "rk4_chain_integrate": (c_int, [H, vp, vp, vp, sz, i64, dp]),
@@ -208,6 +209,12 @@ def rk4_chain_get_tiling(h) -> dict:
     t = rk4_tiling()
     _check(_lib.rk4_chain_get_tiling(h, ctypes.byref(t)), "rk4_chain_get_tiling")
     return _tiling_dict(t)
+
+
+def rk4_chain_get_kernel(h) -> int:
+    k = ctypes.c_int()
+    _check(_lib.rk4_chain_get_kernel(h, ctypes.byref(k)), "rk4_chain_get_kernel")
+    return int(k.value)
 
 
 def rk4_chain_autotune(h, state, comp, ws, probe_steps: int = 16, ws_bytes: int | None = None) -> dict:

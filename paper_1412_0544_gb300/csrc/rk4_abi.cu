@@ -86,15 +86,19 @@ struct rk4_chain {
   // heterogeneous chain (Eq. (1)): caller-owned device array of P parameters per site
   const void *site_params = nullptr;
   unsigned gen_version = 0;  // bumped when the tableau or kappa2 changes (graph cache key)
+  int auto_kernel = RK4_KERNEL_PERSISTENT;  // scheme RK4_KERNEL_AUTO uses for a batch
 };
 
 namespace {
 
 bool use_generic(const rk4_chain *h);
 
+bool use_het(const rk4_chain *h);
+
 int effective_kernel(const rk4_chain *h) {
   if (h->kernel != RK4_KERNEL_AUTO) return h->kernel;
-  return (h->nchains == 1 || use_generic(h)) ? RK4_KERNEL_BLOCKED : RK4_KERNEL_PERSISTENT;
+  if (h->nchains == 1 || use_generic(h) || use_het(h)) return RK4_KERNEL_BLOCKED;
+  return h->auto_kernel;  // batches: persistent unless the autotuner measured the blocked scheme faster
 }
 
 size_t elem_bytes(const rk4_chain *h) { return h->fp32 ? 4 : 8; }
@@ -639,6 +643,12 @@ int rk4_chain_get_tiling(const rk4_chain *h, rk4_tiling *out) {
   return RK4_OK;
 }
 
+int rk4_chain_get_kernel(const rk4_chain *h, int *kernel) {
+  if (!h || !kernel) return RK4_EINVAL;
+  *kernel = effective_kernel(h);
+  return RK4_OK;
+}
+
 int rk4_chain_integrate(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_bytes, int64_t nsteps, double *t) {
   if (!h) return RK4_EINVAL;
   int rc = integrate_impl(h, state, comp, ws, ws_bytes, nsteps);
@@ -782,7 +792,13 @@ int rk4_chain_autotune(rk4_chain *h, void *state, void *comp, void *ws, size_t w
     return RK4_OK;
   }
   if (ws_bytes < layout(h, kernel).total) return RK4_ENOMEM_WS;
+  // a batch left on RK4_KERNEL_AUTO: time the persistent and the blocked scheme and keep the faster
+  const bool choose_kernel = h->kernel == RK4_KERNEL_AUTO && h->nchains > 1 && !use_generic(h) && !use_het(h);
+  const int kernels[2] = {kernel, RK4_KERNEL_BLOCKED};
+  const int nkern = (choose_kernel && kernel != RK4_KERNEL_BLOCKED) ? 2 : 1;
   const rk4_tiling saved = h->tiling;
+  const int saved_auto = h->auto_kernel;
+  int best_kernel = kernel;
   const bool saved_graphs = h->graphs;
   h->graphs = false;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -796,14 +812,17 @@ int rk4_chain_autotune(rk4_chain *h, void *state, void *comp, void *ws, size_t w
   float best_ms = 1e30f;
   rk4_tiling best_t = saved;
   rc = RK4_OK;
+  for (int ki = 0; ki < nkern; ++ki)
   for (int b : blocks)
     for (int v : vs)
       for (int k : ks) {
+        const int kern = kernels[ki];
+        if (choose_kernel) h->auto_kernel = kern;
         if (!tiling_valid(h, b, v, k)) continue;
         if (b == 64 && !use_generic(h)) continue;
         const int maxt = tiling_max_threads(h, v);
         if (maxt <= 0 || b > maxt) continue;
-        if (kernel == RK4_KERNEL_PERSISTENT && persistent_max_grid(h->model, h->fp32, v, b) <= 0) continue;
+        if (kern == RK4_KERNEL_PERSISTENT && persistent_max_grid(h->model, h->fp32, v, b) <= 0) continue;
         h->tiling.block = b;
         h->tiling.v = v;
         h->tiling.k = k;
@@ -823,6 +842,7 @@ int rk4_chain_autotune(rk4_chain *h, void *state, void *comp, void *ws, size_t w
         if (per_step < best_ms) {
           best_ms = per_step;
           best_t = h->tiling;
+          best_kernel = kern;
         }
       }
   cudaEventDestroy(e0);
@@ -830,8 +850,10 @@ int rk4_chain_autotune(rk4_chain *h, void *state, void *comp, void *ws, size_t w
   h->graphs = saved_graphs;
   if (rc != RK4_OK || best_ms >= 1e30f) {
     h->tiling = saved;
+    h->auto_kernel = saved_auto;
     return rc != RK4_OK ? rc : RK4_ECUDA;
   }
+  if (choose_kernel) h->auto_kernel = best_kernel;
   h->tiling = best_t;
   h->tiling_auto = false;
   if (best) *best = best_t;

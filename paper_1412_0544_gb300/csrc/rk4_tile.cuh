@@ -99,8 +99,10 @@ template <bool COH, typename T> __device__ __forceinline__ T gld(const T *p) {
 }
 
 // Copy the W sites starting at chain index t0 (may be negative or run past the end) of the
-// chain at `off` into shared memory, element by element, coalesced.  Periodic: wrapped;
-// fixed: zero outside the chain.
+// chain at `off` into shared memory, coalesced.  Periodic: wrapped; fixed: zero outside the
+// chain.  A tile that crosses a chain end is copied as a few contiguous segments (one index
+// wrap per segment, not per element): at most 2 for chains longer than the tile, N / W + 2
+// for shorter periodic chains.
 template <typename R, int D, bool COH>
 __device__ __forceinline__ void tile_load(R *tile, const R *__restrict__ src, int64_t off, int64_t n, int bc,
                                           int64_t t0, int W) {
@@ -115,19 +117,34 @@ __device__ __forceinline__ void tile_load(R *tile, const R *__restrict__ src, in
     } else {
       for (int e = threadIdx.x; e < total; e += blockDim.x) tile[e] = gld<COH>(s + e);
     }
-  } else {
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-      const int sl = e / D;
-      const int d = e - sl * D;
-      const int64_t g = t0 + sl;
-      R val;
-      if (bc == PERIODIC) {
-        val = gld<COH>(src + (off + wrap(g, n)) * D + d);
-      } else {
-        val = (g >= 0 && g < n) ? gld<COH>(src + (off + g) * D + d) : R(0);
-      }
-      tile[e] = val;
+    return;
+  }
+  int covered = 0;  // block-uniform loop over contiguous segments
+  while (covered < W) {
+    const int64_t g = t0 + covered;
+    const int64_t rest = W - covered;
+    int len;
+    const R *seg = nullptr;  // NULL: a run of fixed-end ghosts (zeros)
+    if (bc == PERIODIC) {
+      const int64_t gw = wrap(g, n);
+      len = (int)(rest < n - gw ? rest : n - gw);
+      seg = src + (off + gw) * D;
+    } else if (g < 0) {
+      len = (int)(rest < -g ? rest : -g);
+    } else if (g >= n) {
+      len = (int)rest;
+    } else {
+      len = (int)(rest < n - g ? rest : n - g);
+      seg = src + (off + g) * D;
     }
+    R *dst = tile + covered * D;
+    const int cnt = len * D;
+    if (seg) {
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) dst[e] = gld<COH>(seg + e);
+    } else {
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) dst[e] = R(0);
+    }
+    covered += len;
   }
 }
 

@@ -345,3 +345,20 @@ def test_integrate_host_buffers(rk, gh):
     rk.rk4_chain_integrate_host(h, host, None, dev, None, ws, 30)
     assert np.array_equal(host.numpy(), ref)
     rk.rk4_chain_destroy(h)
+
+
+def test_batch_autotune_chooses_scheme_and_stays_bitwise(rk, gh, small_batch):
+    """The autotuner may pick the persistent or the blocked scheme for a batch; either way the
+    result is bit for bit the staged kernel's."""
+    import torch
+    lengths, kappa, bcs, y0 = small_batch
+    ref = gh.gpu_run(y0, nsteps=60, lengths=lengths, kappas=kappa, bcs=bcs, kernel=rk.RK4_KERNEL_STAGED)
+    h = rk.rk4_batch_create(ROE, rk.RK4_FP64, lengths, kappa, bcs, 0.01)
+    st = gh.to_dev(y0, torch.float64)
+    ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+    rk.rk4_chain_autotune(h, st.clone(), None, ws, 8)
+    assert rk.rk4_chain_get_kernel(h) in (rk.RK4_KERNEL_PERSISTENT, rk.RK4_KERNEL_BLOCKED)
+    rk.rk4_chain_integrate(h, st, None, ws, 60)
+    torch.cuda.synchronize()
+    assert np.array_equal(st.cpu().numpy(), ref)
+    rk.rk4_chain_destroy(h)
