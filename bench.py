@@ -402,6 +402,43 @@ def variant_extra(rk, torch, stream, precision, *, generic=False, het=False, n=N
         rk.rk4_chain_destroy(h)
 
 
+def harmonic_energy_extra(rk, torch, stream, n=N_SITES, nsteps=NSTEPS, kappa=1.0, omega0=1.0):
+    """Energy behaviour where the chain is Hamiltonian: the periodic harmonic chain (D = 2),
+    N = 2^24, 1000 steps, FP64 and FP32-Kahan; the measured relative drift of the FP64
+    energy reduction next to RK4's exact per-mode energy factor rho(h)^n summed over the
+    Fourier modes of the initial state."""
+    out = {}
+    y0 = None
+    for precision, name in ((rk.RK4_FP64, "fp64"), (rk.RK4_FP32_KAHAN, "fp32_kahan")):
+        fp32 = precision == rk.RK4_FP32_KAHAN
+        h = rk.rk4_chain_create(rk.RK4_HARMONIC, precision, n, DT, rk.RK4_PERIODIC,
+                                dict(kappa=kappa, omega0=omega0), stream)
+        try:
+            st = torch.empty((n, 2), dtype=torch.float32 if fp32 else torch.float64, device="cuda")
+            rk.rk4_fill_uniform(st, n * 2, SEED, 0, precision, stream)
+            if y0 is None:
+                y0 = st.double().cpu().numpy()
+            cp = torch.zeros_like(st) if fp32 else None
+            ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+            e0 = rk.rk4_chain_energy(h, st, cp, ws)[0]
+            el = time_integrate(rk, h, st, cp, ws, nsteps, 1, torch)
+            e1 = rk.rk4_chain_energy(h, st, cp, ws)[0]
+            out[name] = {"site_steps_per_s": n * nsteps / el, "E0": e0, "E_final": e1,
+                         "rel_drift": (e1 - e0) / e0}
+        finally:
+            rk.rk4_chain_destroy(h)
+    # RK4 multiplies each mode's energy by rho(h) = 1 - h^6/72 + h^8/576 per step (h = omega_m dt)
+    m = np.arange(n)
+    w = np.sqrt(omega0 ** 2 + 4.0 * kappa * np.sin(np.pi * m / n) ** 2)
+    qh, ph = np.fft.fft(y0[:, 0]), np.fft.fft(y0[:, 1])
+    em = 0.5 * (np.abs(ph) ** 2 + w ** 2 * np.abs(qh) ** 2) / n
+    hm = w * DT
+    rho = 1.0 - hm ** 6 / 72.0 + hm ** 8 / 576.0
+    out["predicted_rel_drift"] = float(np.sum(em * rho ** nsteps) / np.sum(em) - 1.0)
+    out["N"], out["steps"] = n, nsteps
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -427,8 +464,9 @@ def main():
     from paper_1412_0544_gb300 import dist
     import paper_1412_0544_gb300 as rk
 
+    rank, world, local = dist.env_rank()
+    torch.cuda.set_device(local)  # before the process group, so NCCL binds this rank's GPU
     rank, world, local = dist.init("nccl")
-    torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", HBM_GBS_FALLBACK))
@@ -506,6 +544,7 @@ def main():
         extras["fp32_kahan_2e27"] = fp32_kahan_extra(rk, torch, stream)
         extras["batch_fp64"] = batch_extra(rk, torch, stream, rk.RK4_FP64)
         extras["batch_fp32_kahan"] = batch_extra(rk, torch, stream, rk.RK4_FP32_KAHAN)
+        extras["harmonic_energy"] = harmonic_energy_extra(rk, torch, stream)
         extras["generic_dopri5_nnn_fp64"] = variant_extra(rk, torch, stream, rk.RK4_FP64, generic=True)
         extras["generic_dopri5_nnn_fp32_kahan"] = variant_extra(rk, torch, stream, rk.RK4_FP32_KAHAN, generic=True,
                                                                 nsteps=1000)

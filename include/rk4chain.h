@@ -225,6 +225,12 @@ int rk4_chain_set_option(rk4_chain *h, int option, int64_t value);
 int rk4_debug_barrier_timeout(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_bytes,
                               int64_t timeout_ns);
 
+/* The handle's clock: time origin t0 and steps taken n (t = t0 + n dt).  set_clock restores
+ * both, e.g. when resuming from a checkpoint, so that t stays t0 + n dt with one rounding.
+ * Errors: RK4_EINVAL. */
+int rk4_chain_get_clock(const rk4_chain *h, double *t0, int64_t *nstep);
+int rk4_chain_set_clock(rk4_chain *h, double t0, int64_t nstep);
+
 /* Sets the time origin t0 and resets the step counter. */
 int rk4_chain_set_time(rk4_chain *h, double t0);
 

@@ -71,6 +71,8 @@ def _load():
         "rk4_chain_set_option": (c_int, [H, c_int, i64]),
         "rk4_debug_barrier_timeout": (c_int, [H, vp, vp, vp, sz, i64]),
         "rk4_chain_set_time": (c_int, [H, ctypes.c_double]),
+        "rk4_chain_get_clock": (c_int, [H, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]),
+        "rk4_chain_set_clock": (c_int, [H, ctypes.c_double, i64]),
         "rk4_chain_set_tableau": (c_int, [H, c_int, dp, dp]),
         "rk4_chain_set_coupling2": (c_int, [H, ctypes.c_double]),
         "rk4_chain_set_site_params": (c_int, [H, vp]),
@@ -305,6 +307,18 @@ def rk4_chain_set_site_params(h, params):
     """Per-site parameters of a heterogeneous chain: a device tensor [total_sites, P] in the
     state's precision (P = 4 Roessler a, b, c, kappa; P = 2 harmonic omega^2, kappa), or None."""
     _check(_lib.rk4_chain_set_site_params(h, _ptr(params)), "rk4_chain_set_site_params")
+
+
+def rk4_chain_get_clock(h):
+    """(t0, steps taken): the handle's time is t0 + steps * dt."""
+    t0 = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(_lib.rk4_chain_get_clock(h, ctypes.byref(t0), ctypes.byref(n)), "rk4_chain_get_clock")
+    return t0.value, int(n.value)
+
+
+def rk4_chain_set_clock(h, t0: float, nstep: int):
+    _check(_lib.rk4_chain_set_clock(h, float(t0), int(nstep)), "rk4_chain_set_clock")
 
 
 def rk4_chain_set_time(h, t0: float):

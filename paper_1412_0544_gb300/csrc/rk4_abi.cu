@@ -8,6 +8,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/rk4chain.h"
 #include "rk4_internal.h"
 
@@ -649,8 +651,15 @@ int rk4_chain_get_kernel(const rk4_chain *h, int *kernel) {
   return RK4_OK;
 }
 
+// NVTX range around a host-side call (visible in Nsight timelines; no cost without a tool).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 int rk4_chain_integrate(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_bytes, int64_t nsteps, double *t) {
   if (!h) return RK4_EINVAL;
+  NvtxRange range("rk4_chain_integrate");
   int rc = integrate_impl(h, state, comp, ws, ws_bytes, nsteps);
   if (rc == RK4_OK) {
     h->nstep += nsteps;
@@ -684,6 +693,7 @@ int rk4_chain_integrate_host(rk4_chain *h, void *host_state, void *host_comp, vo
 
 int rk4_chain_energy(rk4_chain *h, const void *state, const void *comp, void *ws, size_t ws_bytes, double *out) {
   if (!h || !out) return RK4_EINVAL;
+  NvtxRange range("rk4_chain_energy");
   if (use_het(h) && h->model == RK4_HARMONIC) return RK4_EUNSUPPORTED;
   int rc = check_buffers(h, state, comp, ws);
   if (rc) return rc;
@@ -784,6 +794,7 @@ int rk4_debug_barrier_timeout(rk4_chain *h, void *state, void *comp, void *ws, s
 int rk4_chain_autotune(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_bytes, int probe_steps,
                        rk4_tiling *best) {
   if (!h || probe_steps < 1 || probe_steps > 100000) return RK4_EINVAL;
+  NvtxRange range("rk4_chain_autotune");
   int rc = check_buffers(h, state, comp, ws);
   if (rc) return rc;
   const int kernel = effective_kernel(h);
@@ -902,6 +913,20 @@ int rk4_chain_set_site_params(rk4_chain *h, const void *params) {
   if (params && (reinterpret_cast<uintptr_t>(params) % 16) != 0) return RK4_EINVAL;
   h->site_params = params;
   default_tiling(h);
+  return RK4_OK;
+}
+
+int rk4_chain_get_clock(const rk4_chain *h, double *t0, int64_t *nstep) {
+  if (!h) return RK4_EINVAL;
+  if (t0) *t0 = h->t0;
+  if (nstep) *nstep = h->nstep;
+  return RK4_OK;
+}
+
+int rk4_chain_set_clock(rk4_chain *h, double t0, int64_t nstep) {
+  if (!h || !std::isfinite(t0) || nstep < 0) return RK4_EINVAL;
+  h->t0 = t0;
+  h->nstep = nstep;
   return RK4_OK;
 }
 

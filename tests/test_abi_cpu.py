@@ -196,3 +196,20 @@ def test_site_params_validation(rk):
         rk.rk4_chain_set_tiling(h, 128, 8, 1)
     finally:
         rk.rk4_chain_destroy(h)
+
+
+def test_checkpoint_file_round_trip(rk, tmp_path):
+    from paper_1412_0544_gb300 import checkpoint
+    st = np.arange(30, dtype=np.float32).reshape(10, 3)
+    cp = st * 1e-7
+    p = str(tmp_path / "c.npz")
+    checkpoint.save(p, st, cp, t0=1.5, nstep=42, model="roessler", n=10)
+    s2, c2, meta = checkpoint.load(p)
+    assert np.array_equal(s2, st) and np.array_equal(c2, cp)
+    assert meta["t0"] == 1.5 and meta["nstep"] == 42 and meta["model"] == "roessler"
+    h = rk.rk4_chain_create(0, 1, 10, 0.01, 0)
+    rk.rk4_chain_set_clock(h, 1.5, 42)
+    assert rk.rk4_chain_get_clock(h) == (1.5, 42)
+    with pytest.raises(rk.RK4Error):
+        rk.rk4_chain_set_clock(h, 0.0, -1)
+    rk.rk4_chain_destroy(h)

@@ -362,3 +362,39 @@ def test_batch_autotune_chooses_scheme_and_stays_bitwise(rk, gh, small_batch):
     torch.cuda.synchronize()
     assert np.array_equal(st.cpu().numpy(), ref)
     rk.rk4_chain_destroy(h)
+
+
+def test_checkpoint_resume_bitwise(rk, tmp_path):
+    """integrate a steps, checkpoint, resume in a fresh handle, integrate b: bit-identical to
+    a + b steps in one call, with the same clock (FP32-Kahan, so the compensation matters)."""
+    import torch
+    from paper_1412_0544_gb300 import checkpoint
+    y0 = ci.uniform_state(30011, 3, seed=99).astype(np.float32)
+    prec = rk.RK4_FP32_KAHAN
+
+    def fresh():
+        h = rk.rk4_chain_create(ROE, prec, y0.shape[0], 0.01, PER)
+        ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+        return h, ws
+
+    h, ws = fresh()
+    st = torch.from_numpy(y0).cuda()
+    cp = torch.zeros_like(st)
+    t_full = rk.rk4_chain_integrate(h, st, cp, ws, 70)
+    full = (st.cpu().numpy(), cp.cpu().numpy())
+    rk.rk4_chain_destroy(h)
+
+    h, ws = fresh()
+    st = torch.from_numpy(y0).cuda()
+    cp = torch.zeros_like(st)
+    rk.rk4_chain_integrate(h, st, cp, ws, 25)
+    path = str(tmp_path / "chk.npz")
+    checkpoint.save_handle(path, rk, h, st, cp, model="roessler")
+    rk.rk4_chain_destroy(h)
+
+    h, ws = fresh()
+    st2, cp2, meta = checkpoint.restore_handle(path, rk, h)
+    t_resumed = rk.rk4_chain_integrate(h, st2, cp2, ws, 45)
+    rk.rk4_chain_destroy(h)
+    assert meta["nstep"] == 25 and t_resumed == t_full
+    assert np.array_equal(st2.cpu().numpy(), full[0]) and np.array_equal(cp2.cpu().numpy(), full[1])
