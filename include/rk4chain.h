@@ -213,7 +213,8 @@ int rk4_chain_status(rk4_chain *h, void *ws);
 
 /* Options (enum rk4_option): RK4_OPT_GRAPHS (1 = replay launch sequences from a cached CUDA
  * graph, the default; 0 = launch directly), RK4_OPT_TIMEOUT_NS (bound on any device-side
- * barrier wait of the persistent kernel, default 2e9 ns).  Errors: RK4_EINVAL. */
+ * barrier wait of the persistent kernel; by default 2e9 ns or 20 ns per site-step of one time
+ * block, whichever is larger).  Errors: RK4_EINVAL. */
 enum rk4_option { RK4_OPT_GRAPHS = 0, RK4_OPT_TIMEOUT_NS = 1 };
 int rk4_chain_set_option(rk4_chain *h, int option, int64_t value);
 

@@ -89,6 +89,7 @@ struct rk4_chain {
   const void *site_params = nullptr;
   unsigned gen_version = 0;  // bumped when the tableau or kappa2 changes (graph cache key)
   int auto_kernel = RK4_KERNEL_PERSISTENT;  // scheme RK4_KERNEL_AUTO uses for a batch
+  bool timeout_set = false;                 // RK4_OPT_TIMEOUT_NS given explicitly
 };
 
 namespace {
@@ -407,7 +408,15 @@ cudaError_t enqueue_integrate(rk4_chain *h, int kernel, void *state, void *comp,
     j.ntail = (int)P.tail.size();
     for (int i = 0; i < j.ntail; ++i) j.tail[i] = P.tail[i];
     j.hdr = reinterpret_cast<WsHeader *>(ws + L.hdr);
-    j.timeout_ns = h->timeout_ns;
+    // A barrier waits at most one time block; unless the caller set the bound, allow 20x a
+    // pessimistic estimate of one (1e9 site-steps/s) so that very large batches cannot time
+    // out spuriously.
+    {
+      int kmax = 1;
+      for (int kv : P.kval) kmax = std::max(kmax, kv);
+      const double est_ns = (double)h->total * kmax;  // at 1e9 site-steps/s: 1 ns per site-step
+      j.timeout_ns = h->timeout_set ? h->timeout_ns : std::max<long long>(h->timeout_ns, (long long)(20.0 * est_ns));
+    }
     j.extra_arrivals = 0;
     int grid = persistent_max_grid(h->model, h->fp32, h->tiling.v, h->tiling.block);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
@@ -744,6 +753,7 @@ int rk4_chain_set_option(rk4_chain *h, int option, int64_t value) {
   if (option == RK4_OPT_TIMEOUT_NS) {
     if (value < 1000 || value > (int64_t)600 * 1000000000LL) return RK4_EINVAL;
     h->timeout_ns = value;
+    h->timeout_set = true;
     return RK4_OK;
   }
   return RK4_EINVAL;
