@@ -63,7 +63,15 @@ __global__ void __launch_bounds__(max_threads_for(V), (V >= 8 && KAHAN) ? 2 : 1)
     R *out = static_cast<R *>((t & 1) ? job.bufA : job.bufB);
     const R *cin = static_cast<const R *>((t & 1) ? job.cB : job.cA);
     R *cout = static_cast<R *>((t & 1) ? job.cA : job.cB);
-    for (int64_t item = blockIdx.x; item < ntiles; item += gridDim.x) {
+    // Items are handed out dynamically (an atomic counter per time-block parity), so blocks
+    // that drew cheaper items take more and all reach the barrier together.  Block 0 clears
+    // the other parity's counter for the next time block (the barrier orders it).
+    unsigned long long *ctr = &job.hdr->work[t & 1];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && t > 0) job.hdr->work[(t + 1) & 1] = 0ull;
+    __shared__ long long s_item;
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(ctr, 1ull);
+    __syncthreads();
+    for (int64_t item = s_item; item < ntiles;) {
       ChainDesc ch;
       int64_t tile = item;
       Coef<R> c = cf;
@@ -76,6 +84,10 @@ __global__ void __launch_bounds__(max_threads_for(V), (V >= 8 && KAHAN) ? 2 : 1)
         c.kappa = (R)ch.kappa;
       }
       tile_item<R, MODEL, V, KAHAN, true>(in, out, cin, cout, ch, tile, K, G, c, smem);
+      // tile_item ends with a barrier, so every thread has read s_item before it is rewritten
+      if (threadIdx.x == 0) s_item = (long long)atomicAdd(ctr, 1ull);
+      __syncthreads();
+      item = s_item;
     }
     if (t + 1 < nblocks_t || job.extra_arrivals > 0) {
       if (!grid_barrier(job.hdr, job.timeout_ns, job.extra_arrivals)) return;

@@ -39,7 +39,8 @@ struct WsHeader {
   unsigned bar_count;
   unsigned bar_gen;
   int timeout_where;
-  unsigned char pad[240];
+  unsigned long long work[2];  // persistent kernel: next item of the current time block, by parity
+  unsigned char pad[224];
 };
 
 // Arguments of one blocked launch (one chain, or a batch through a chain table).
