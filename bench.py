@@ -55,8 +55,8 @@ FP32K_INST_PER_SITE_STEP = 61    # + 4 per component for the Kahan update
 # DRAM traffic (read + write bytes) per launch of the FP64 blocked kernel at N = 2^24 from one
 # ncu --set full capture, valid only for the kernel sources (hash) and the tiling recorded with
 # it; any other combination reports null.
-TRAFFIC = {("d92f26e96980e065", "256,4,1"): 402767360 + 357237760,
-           ("d92f26e96980e065", "256,4,2"): 402888448 + 356931584}
+TRAFFIC = {("a2728451cc16c09e", "256,4,1"): 403167744 + 357529856,
+           ("a2728451cc16c09e", "256,4,2"): 402814976 + 357812224}
 
 
 def kernel_hash() -> str:
