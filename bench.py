@@ -44,11 +44,12 @@ HBM_GBS_FALLBACK = 6800.0
 # FP64 issue rates measured on this GPU model with independent dependency chains (8 per
 # thread, 4 blocks of 256 threads per SM): DFMA 0.5957e12/s, DADD and DMUL 0.5051e12/s; FP32
 # FMA 36.6e12/s.  The classical RK4 Roessler step issues 34 DFMA and 15 DADD per site-step
-# (4 x (4 FMA + 3 ADD) slope, 9 FMA stage states, 6 FMA + 3 ADD sum, 3 FMA update), so its FP64
-# roof is the harmonic mix of the two rates (a 2:1 DFMA:DADD probe measured 0.5652e12/s).
+# (4 x (4 FMA + 3 ADD) slope, 9 FMA stage states, 6 FMA + 3 ADD sum, 3 FMA update).  Every
+# addition can be issued as an exact FMA (a*1+b), so 49 instructions at the DFMA rate bound
+# the step; a variant built that way gave the same bits and the same time, so the slower DADD
+# rate is not the floor and the roof is the DFMA rate.
 FP64_DFMA_PEAK = 0.5957e12
-FP64_DADD_PEAK = 0.5051e12
-FP64_INST_PEAK = 1.0 / (34 / 49 / FP64_DFMA_PEAK + 15 / 49 / FP64_DADD_PEAK)
+FP64_INST_PEAK = FP64_DFMA_PEAK
 FP32_INST_PEAK = 36.6e12
 FP64_INST_PER_SITE_STEP = 49     # 34 DFMA + 15 DADD
 FP32K_INST_PER_SITE_STEP = 61    # + 4 per component for the Kahan update
@@ -524,8 +525,8 @@ def main():
                 "traffic": traffic, "kernel": "k_blocked<double, Roessler>",
                 "per_unit": "49 FP64 instructions per interior site-step",
                 "launch_ms": launch_s * 1e3,
-                "peak_source": "of measured: FP64 issue rate for this kernel's 34:15 DFMA:DADD mix, from the "
-                               "measured DFMA (0.596e12/s) and DADD (0.505e12/s) rates",
+                "peak_source": "of measured: DFMA issue rate (0.596e12/s); all 49 operations of the step "
+                               "can issue as DFMA",
                 "hbm_frac_effective_state": sps_k * 2 * D * 8 / 1e9 / hbm_peak}
 
     # --- end to end through the C ABI with host buffers ------------------------------
