@@ -408,6 +408,45 @@ def variant_extra(rk, torch, stream, precision, *, generic=False, het=False, n=N
         rk.rk4_chain_destroy(h)
 
 
+def domain_extra(rk, torch, stream, precision, nparts=4, ghost=32, n=N_SITES, nsteps=200):
+    """The N = 2^24 periodic Roessler chain split into `nparts` sub-domains with `ghost` sites of
+    ghost zone per side (classical RK4 reaches 4 sites per step: ghost / 4 steps between
+    device-to-device ghost exchanges), against the undivided chain at the same tiling."""
+    fp32 = precision == rk.RK4_FP32_KAHAN
+    dtype = torch.float32 if fp32 else torch.float64
+    d = rk.rk4_domain_create(rk.RK4_ROESSLER, precision, n, DT, rk.RK4_PERIODIC, nparts, ghost, None, None, stream)
+    h = rk.rk4_chain_create(rk.RK4_ROESSLER, precision, n, DT, rk.RK4_PERIODIC, None, stream)
+    try:
+        tiling = rk.rk4_chain_get_tiling(rk.rk4_domain_chain(d))
+        rk.rk4_chain_set_tiling(h, tiling["block"], tiling["v"], tiling["k"])
+        cst = torch.empty((n, D), dtype=dtype, device="cuda")
+        rk.rk4_fill_uniform(cst, n * D, SEED, 0, precision, stream)
+        ccp = torch.zeros_like(cst) if fp32 else None
+        rows, _ = rk.rk4_domain_shape(d)
+        st = torch.empty((rows, D), dtype=dtype, device="cuda")
+        cp = torch.zeros_like(st) if fp32 else None
+        ws = torch.empty(rk.rk4_domain_workspace_bytes(d), dtype=torch.uint8, device="cuda")
+        rk.rk4_domain_scatter(d, cst, ccp, st, cp)
+        rk.rk4_domain_integrate(d, st, cp, ws, 2 * ghost)  # warm-up (graphs)
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        rk.rk4_domain_integrate(d, st, cp, ws, nsteps)
+        e1.record(s)
+        e1.synchronize()
+        el = e0.elapsed_time(e1) / 1e3
+        wsw = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+        rk.rk4_chain_integrate(h, cst, ccp, wsw, 2 * ghost)
+        el_whole = time_integrate(rk, h, cst, ccp, wsw, nsteps, 1, torch)
+        return {"value": n * nsteps / el, "unit": "site-steps/s", "N": n, "steps": nsteps, "parts": nparts,
+                "ghost": ghost, "steps_per_exchange": ghost // 4, "tiling": tiling,
+                "undivided_same_tiling": n * nsteps / el_whole, "ratio_to_undivided": el_whole / el}
+    finally:
+        rk.rk4_chain_destroy(h)
+        rk.rk4_domain_destroy(d)
+
+
 def harmonic_energy_extra(rk, torch, stream, n=N_SITES, nsteps=NSTEPS, kappa=1.0, omega0=1.0):
     """Energy behaviour where the chain is Hamiltonian: the periodic harmonic chain (D = 2),
     N = 2^24, 1000 steps, FP64 and FP32-Kahan; the measured relative drift of the FP64
@@ -558,6 +597,8 @@ def main():
         extras["heterogeneous_fp64"] = variant_extra(rk, torch, stream, rk.RK4_FP64, het=True)
         extras["heterogeneous_fp32_kahan"] = variant_extra(rk, torch, stream, rk.RK4_FP32_KAHAN, het=True,
                                                            nsteps=1000)
+        extras["domain_4parts_fp64"] = domain_extra(rk, torch, stream, rk.RK4_FP64)
+        extras["domain_4parts_fp32_kahan"] = domain_extra(rk, torch, stream, rk.RK4_FP32_KAHAN, nsteps=1000)
     rk.rk4_chain_destroy(h)
 
     out = None

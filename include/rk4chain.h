@@ -248,6 +248,91 @@ const char *rk4_strerror(int code);
 int rk4_fill_uniform(void *dst, int64_t count, uint64_t seed, uint64_t start, int precision,
                      void *cuda_stream);
 
+/* ---- Sub-domain decomposition of one chain --------------------------------------------------
+ * One chain of n sites split into nparts contiguous parts, each stored with ghost zones of
+ * `ghost` sites per side and integrated as an independent fixed-end chain between ghost
+ * exchanges: Sec. 2.3's granularity with overlap (a cluster plus s sites of overlap per side
+ * per step, recomputed redundantly) applied to memory partitions -- the form a chain takes
+ * when it is spread over several memories, with one neighbour exchange every few steps.
+ * An s-stage scheme with coupling range r moves information s r sites per step, so the
+ * parts run floor(ghost / (s r)) steps between exchanges (ghost / 4 for classical RK4 with
+ * nearest neighbours), and every interior site performs the same operations as in the
+ * undivided chain: the gathered result is bit-identical to rk4_chain_integrate on the whole
+ * chain with the same model, precision, parameters and tableau.
+ *
+ * Domain state layout: the parts' blocks back to back, part p occupying rows
+ * [row_p, row_p + ghost_left_p + sites_p + ghost_right_p) of a [rows][D] array in the chain's
+ * precision: its left ghost zone, its sites first_site_p .. first_site_p + sites_p - 1, its
+ * right ghost zone.  Every part has both ghost zones except the first (no left) and the last
+ * (no right) part of a fixed-end chain.  comp (RK4_FP32_KAHAN) has the same layout.  Buffers
+ * are caller-owned device memory, 16-byte aligned; ws 256-byte aligned.  Calls are
+ * stream-ordered on the domain's stream unless they say they synchronise.  Ghost copies are
+ * device-to-device cudaMemcpyAsync calls, one per ghost zone and array. */
+typedef struct rk4_domain rk4_domain; /* opaque host-side handle */
+
+/* Creates a domain over one chain (model, precision, n, dt, bc, p, cuda_stream as for
+ * rk4_chain_create).  nparts >= 1 parts; part_lengths (host, nparts entries summing to n,
+ * copied) gives each part's sites, or NULL for an even split (the first n % nparts parts one
+ * site longer).  ghost >= 1 sites per ghost zone (0 allowed only for one part of a fixed-end
+ * chain, which has none), and every part at least `ghost` sites long when ghost zones exist.
+ * The parts are integrated by one batch handle of fixed-end chains (RK4_KERNEL_BLOCKED unless
+ * changed through rk4_domain_chain).  Errors: RK4_EINVAL. */
+int rk4_domain_create(rk4_domain **out, int model, int precision, int64_t n, double dt, int bc,
+                      const rk4_params *p, int nparts, const int64_t *part_lengths, int64_t ghost,
+                      void *cuda_stream);
+
+/* Where part `part` lives: its first chain site and site count, its first row in the domain
+ * state, and its ghost zone widths (any pointer may be NULL).  Errors: RK4_EINVAL. */
+int rk4_domain_part(const rk4_domain *d, int part, int64_t *first_site, int64_t *sites, int64_t *row,
+                    int64_t *ghost_left, int64_t *ghost_right);
+
+/* Rows of the domain state (sites plus ghost zones of all parts) and D. */
+int rk4_domain_shape(const rk4_domain *d, int64_t *rows, int *dim);
+
+/* The batch handle that integrates the parts, owned by the domain (do not destroy it, and do
+ * not integrate it directly: that skips the exchanges).  Use it to choose the kernel and the
+ * tiling, a tableau or second-neighbour coupling, and options; a tableau or coupling range
+ * whose reach s r exceeds the ghost width makes rk4_domain_integrate return
+ * RK4_EUNSUPPORTED.  Errors: RK4_EINVAL. */
+int rk4_domain_chain(rk4_domain *d, rk4_chain **parts);
+
+/* Bytes of workspace rk4_domain_integrate and rk4_domain_energy need (the batch handle's
+ * workspace for its current kernel and tiling, plus reduction scratch). */
+int rk4_domain_workspace_bytes(const rk4_domain *d, size_t *bytes);
+
+/* Copies a whole-chain state [n][D] (and comp) into the domain layout, ghost zones included.
+ * Errors: RK4_EINVAL, RK4_ECUDA. */
+int rk4_domain_scatter(rk4_domain *d, const void *chain_state, const void *chain_comp, void *state,
+                       void *comp);
+
+/* Copies the parts' sites (not the ghosts) back into a whole-chain state [n][D] (and comp).
+ * Errors: RK4_EINVAL, RK4_ECUDA. */
+int rk4_domain_gather(rk4_domain *d, const void *state, const void *comp, void *chain_state,
+                      void *chain_comp);
+
+/* Refreshes every ghost zone from the neighbouring part's sites (cyclically for periodic
+ * ends).  Errors: RK4_EINVAL, RK4_ECUDA. */
+int rk4_domain_exchange(rk4_domain *d, void *state, void *comp);
+
+/* Advances the domain nsteps >= 0 steps: exchange the ghosts, integrate every part
+ * floor(ghost / (s r)) steps (fewer at the end), repeat.  t as for rk4_chain_integrate.
+ * Errors: RK4_EINVAL, RK4_ENOMEM_WS, RK4_ECUDA, RK4_EUNSUPPORTED (heterogeneous parameters
+ * set on the batch handle, or a scheme whose reach per step exceeds the ghost width). */
+int rk4_domain_integrate(rk4_domain *d, void *state, void *comp, void *ws, size_t ws_bytes,
+                         int64_t nsteps, double *t);
+
+/* The whole chain's FP64 energy or half squared norm (as rk4_chain_energy), summed part by
+ * part over the parts' sites after a ghost exchange, so that bonds across part boundaries are
+ * counted once.  Synchronises the stream.  Returns RK4_ENONFINITE if a NaN or infinity was
+ * seen; RK4_EUNSUPPORTED if the coupling range exceeds the ghost width. */
+int rk4_domain_energy(rk4_domain *d, void *state, void *comp, void *ws, size_t ws_bytes, double *out);
+
+/* rk4_chain_status of the parts' batch handle on ws (the most recent integration period). */
+int rk4_domain_status(rk4_domain *d, void *ws);
+
+/* Frees the domain and its batch handle.  NULL is accepted. */
+int rk4_domain_destroy(rk4_domain *d);
+
 #ifdef __cplusplus
 }
 #endif

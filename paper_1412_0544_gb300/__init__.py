@@ -79,6 +79,19 @@ def _load():
         "rk4_chain_destroy": (c_int, [H]),
         "rk4_strerror": (ctypes.c_char_p, [c_int]),
         "rk4_fill_uniform": (c_int, [vp, i64, ctypes.c_uint64, ctypes.c_uint64, c_int, vp]),
+        "rk4_domain_create": (c_int, [ctypes.POINTER(H), c_int, c_int, i64, ctypes.c_double, c_int,
+                                      ctypes.POINTER(rk4_params), c_int, ctypes.POINTER(i64), i64, vp]),
+        "rk4_domain_part": (c_int, [H, c_int] + [ctypes.POINTER(i64)] * 5),
+        "rk4_domain_shape": (c_int, [H, ctypes.POINTER(i64), ctypes.POINTER(c_int)]),
+        "rk4_domain_chain": (c_int, [H, ctypes.POINTER(H)]),
+        "rk4_domain_workspace_bytes": (c_int, [H, ctypes.POINTER(sz)]),
+        "rk4_domain_scatter": (c_int, [H, vp, vp, vp, vp]),
+        "rk4_domain_gather": (c_int, [H, vp, vp, vp, vp]),
+        "rk4_domain_exchange": (c_int, [H, vp, vp]),
+        "rk4_domain_integrate": (c_int, [H, vp, vp, vp, sz, i64, dp]),
+        "rk4_domain_energy": (c_int, [H, vp, vp, vp, sz, dp]),
+        "rk4_domain_status": (c_int, [H, vp]),
+        "rk4_domain_destroy": (c_int, [H]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -334,6 +347,86 @@ def rk4_fill_uniform(dst, count: int, seed: int, start: int = 0, precision: int 
     _check(_lib.rk4_fill_uniform(_ptr(dst), int(count), int(seed) & 0xFFFFFFFFFFFFFFFF,
                                  int(start) & 0xFFFFFFFFFFFFFFFF, int(precision), _stream(stream)),
            "rk4_fill_uniform")
+
+
+def rk4_domain_create(model: int, precision: int, n: int, dt: float, bc: int, nparts: int, ghost: int,
+                      part_lengths=None, params=None, stream=None):
+    """One chain split into `nparts` parts with `ghost` sites of ghost zone per side (see
+    rk4_domain_part for the layout); part_lengths None splits evenly."""
+    h = ctypes.c_void_p()
+    p = _params(params)
+    pl = None
+    if part_lengths is not None:
+        arr = np.ascontiguousarray(part_lengths, dtype=np.int64)
+        if arr.shape != (int(nparts),):
+            raise ValueError("part_lengths needs one entry per part")
+        pl = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    _check(_lib.rk4_domain_create(ctypes.byref(h), int(model), int(precision), int(n), float(dt), int(bc),
+                                  ctypes.byref(p), int(nparts), pl, int(ghost), _stream(stream)), "rk4_domain_create")
+    return h
+
+
+def rk4_domain_part(d, part: int) -> dict:
+    v = [ctypes.c_int64() for _ in range(5)]
+    _check(_lib.rk4_domain_part(d, int(part), *[ctypes.byref(x) for x in v]), "rk4_domain_part")
+    return dict(zip(("first_site", "sites", "row", "ghost_left", "ghost_right"), (int(x.value) for x in v)))
+
+
+def rk4_domain_shape(d):
+    rows = ctypes.c_int64()
+    dim = ctypes.c_int()
+    _check(_lib.rk4_domain_shape(d, ctypes.byref(rows), ctypes.byref(dim)), "rk4_domain_shape")
+    return int(rows.value), int(dim.value)
+
+
+def rk4_domain_chain(d):
+    """The batch handle that integrates the parts (owned by the domain: never destroy it)."""
+    h = ctypes.c_void_p()
+    _check(_lib.rk4_domain_chain(d, ctypes.byref(h)), "rk4_domain_chain")
+    return h
+
+
+def rk4_domain_workspace_bytes(d) -> int:
+    b = ctypes.c_size_t()
+    _check(_lib.rk4_domain_workspace_bytes(d, ctypes.byref(b)), "rk4_domain_workspace_bytes")
+    return int(b.value)
+
+
+def rk4_domain_scatter(d, chain_state, chain_comp, state, comp):
+    _check(_lib.rk4_domain_scatter(d, _ptr(chain_state), _ptr(chain_comp), _ptr(state), _ptr(comp)),
+           "rk4_domain_scatter")
+
+
+def rk4_domain_gather(d, state, comp, chain_state, chain_comp):
+    _check(_lib.rk4_domain_gather(d, _ptr(state), _ptr(comp), _ptr(chain_state), _ptr(chain_comp)),
+           "rk4_domain_gather")
+
+
+def rk4_domain_exchange(d, state, comp):
+    _check(_lib.rk4_domain_exchange(d, _ptr(state), _ptr(comp)), "rk4_domain_exchange")
+
+
+def rk4_domain_integrate(d, state, comp, ws, nsteps: int, ws_bytes: int | None = None) -> float:
+    t = ctypes.c_double()
+    wb = _nbytes(ws) if ws_bytes is None else ws_bytes
+    _check(_lib.rk4_domain_integrate(d, _ptr(state), _ptr(comp), _ptr(ws), wb, int(nsteps), ctypes.byref(t)),
+           "rk4_domain_integrate")
+    return t.value
+
+
+def rk4_domain_energy(d, state, comp, ws, ws_bytes: int | None = None) -> float:
+    out = ctypes.c_double()
+    wb = _nbytes(ws) if ws_bytes is None else ws_bytes
+    _check(_lib.rk4_domain_energy(d, _ptr(state), _ptr(comp), _ptr(ws), wb, ctypes.byref(out)), "rk4_domain_energy")
+    return out.value
+
+
+def rk4_domain_status(d, ws) -> int:
+    return int(_lib.rk4_domain_status(d, _ptr(ws)))
+
+
+def rk4_domain_destroy(d):
+    _check(_lib.rk4_domain_destroy(d), "rk4_domain_destroy")
 
 
 from .chain import Chain  # noqa: E402  (convenience wrapper over the functions above)

@@ -61,14 +61,15 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
   return v;  // valid in thread 0
 }
 
+// Sum over the chain-local sites [lo, hi) of one chain (the whole chain: lo = 0, hi = n).
 template <int MODEL, typename R>
-__global__ void __launch_bounds__(256) k_energy_chain(const R *y, const R *c, ChainDesc ch, double w2,
-                                                      double kappa2, double *partials, WsHeader *hdr) {
+__global__ void __launch_bounds__(256) k_energy_chain(const R *y, const R *c, ChainDesc ch, int64_t lo, int64_t hi,
+                                                      double w2, double kappa2, double *partials, WsHeader *hdr) {
   __shared__ double red[32];
   bool bad = false;
   double acc = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ch.n; i += stride)
+  for (int64_t i = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += stride)
     acc += site_energy<MODEL>(y, c, ch, w2, kappa2, i, bad);
   if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(&hdr->status, ST_NONFINITE);
   const double s = block_sum(acc, red);
@@ -104,7 +105,7 @@ static cudaError_t energy_t(const void *state, const void *cmp, int nchains, con
   const R *y = static_cast<const R *>(state);
   const R *c = static_cast<const R *>(cmp);
   if (nchains == 1) {
-    k_energy_chain<MODEL, R><<<kEnergyBlocks, 256, 0, st>>>(y, c, one, cf.w2, cf.kappa2, partials, hdr);
+    k_energy_chain<MODEL, R><<<kEnergyBlocks, 256, 0, st>>>(y, c, one, 0, one.n, cf.w2, cf.kappa2, partials, hdr);
     k_energy_final<<<1, 1024, 0, st>>>(partials, kEnergyBlocks, out);
   } else {
     k_energy_batch<MODEL, R><<<nchains, 256, 0, st>>>(y, c, chains, cf.w2, cf.kappa2, out, hdr);
@@ -120,6 +121,25 @@ cudaError_t launch_energy(int model, bool fp32, const void *state, const void *c
                 : energy_t<ROESSLER, double>(state, cmp, nchains, one, chains, cf, partials, out, hdr, st);
   return fp32 ? energy_t<HARMONIC, float>(state, cmp, nchains, one, chains, cf, partials, out, hdr, st)
               : energy_t<HARMONIC, double>(state, cmp, nchains, one, chains, cf, partials, out, hdr, st);
+}
+
+template <int MODEL, typename R>
+static cudaError_t energy_range_t(const void *state, const void *cmp, const ChainDesc &ch, int64_t lo, int64_t hi,
+                                  const CoefD &cf, double *partials, double *out, WsHeader *hdr, cudaStream_t st) {
+  k_energy_chain<MODEL, R><<<kEnergyBlocks, 256, 0, st>>>(static_cast<const R *>(state), static_cast<const R *>(cmp),
+                                                          ch, lo, hi, cf.w2, cf.kappa2, partials, hdr);
+  k_energy_final<<<1, 1024, 0, st>>>(partials, kEnergyBlocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_range(int model, bool fp32, const void *state, const void *cmp, const ChainDesc &ch,
+                                int64_t lo, int64_t hi, const CoefD &cf, double *partials, double *out,
+                                WsHeader *hdr, cudaStream_t st) {
+  if (model == ROESSLER)
+    return fp32 ? energy_range_t<ROESSLER, float>(state, cmp, ch, lo, hi, cf, partials, out, hdr, st)
+                : energy_range_t<ROESSLER, double>(state, cmp, ch, lo, hi, cf, partials, out, hdr, st);
+  return fp32 ? energy_range_t<HARMONIC, float>(state, cmp, ch, lo, hi, cf, partials, out, hdr, st)
+              : energy_range_t<HARMONIC, double>(state, cmp, ch, lo, hi, cf, partials, out, hdr, st);
 }
 
 // SplitMix64 output function (Steele, Lea and Flood, OOPSLA 2014) applied to state x.

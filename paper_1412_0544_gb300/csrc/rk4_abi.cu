@@ -546,6 +546,13 @@ int rk4d::handle_info(const rk4_chain *h, int *model, bool *fp32, int *nchains, 
   return RK4_OK;
 }
 
+int rk4d::scheme_reach(const rk4_chain *h, int *s, int *range) {
+  if (!h) return RK4_EINVAL;
+  *s = stages(h);
+  *range = coupling_range(h);
+  return RK4_OK;
+}
+
 extern "C" {
 
 void rk4_params_default(rk4_params *p) {

@@ -115,6 +115,11 @@ int persistent_max_grid(int model, bool fp32, int v, int block);
 cudaError_t launch_energy(int model, bool fp32, const void *state, const void *cmp, int nchains,
                           const ChainDesc &one, const ChainDesc *chains, const CoefD &cf, double *partials,
                           double *out, WsHeader *hdr, cudaStream_t st);
+// Energy of the chain-local sites [lo, hi) of one chain; neighbours outside the range are read
+// from the state like any other site (a sub-domain's ghost zones).  out: one device double.
+cudaError_t launch_energy_range(int model, bool fp32, const void *state, const void *cmp, const ChainDesc &ch,
+                                int64_t lo, int64_t hi, const CoefD &cf, double *partials, double *out,
+                                WsHeader *hdr, cudaStream_t st);
 cudaError_t launch_fill_uniform(void *dst, int64_t count, uint64_t seed, uint64_t start, bool fp32,
                                 cudaStream_t st);
 cudaError_t launch_gen_staged_step(int model, bool fp32, int range, const GenStagedJob &job, const CoefD &cf,
@@ -135,5 +140,8 @@ namespace rk4d {
 // Read-only view of a handle (model, precision, chain table on the host, coefficients, stream).
 int handle_info(const rk4_chain *h, int *model, bool *fp32, int *nchains, const ChainDesc **chains, CoefD *cf,
                 cudaStream_t *stream, bool *het);
+// Stages of the handle's tableau and its coupling range (1, or 2 with second neighbours): one
+// step reaches stages x range sites along the chain.
+int scheme_reach(const rk4_chain *h, int *stages, int *range);
 
 }  // namespace rk4d

@@ -1,9 +1,15 @@
-"""Multi-process helpers for the benchmark: one process per GPU, independent work per rank.
+"""Multi-process helpers: one process per GPU.
 
-The chains of a batch are independent, and so are replicas of a single-chain workload, so
-ranks exchange no data on the hot path: the only collectives are a barrier around the timed
-region and a max-reduction of the elapsed time.  (A single chain split across GPUs would need
-one halo exchange of 4k sites per side every k steps; that form is not built.)
+The chains of a batch are independent, and so are replicas of a single-chain workload, so the
+benchmark's ranks exchange no data on the hot path: the only collectives are a barrier around
+the timed region and a max-reduction of the elapsed time.
+
+A single chain split across ranks is the sub-domain decomposition of the library's
+rk4_domain_* calls with one part per rank: each rank holds its part with ghost zones (the
+library's layout, from rk4_domain_part) and integrates it as a fixed-end chain; every
+floor(ghost / reach) steps the ranks swap ghost zones with their neighbours by point-to-point
+messages (exchange_ghosts, integrate_decomposed).  reach = stages x coupling range sites per
+step (4 for classical RK4 with nearest neighbours).
 """
 from __future__ import annotations
 
@@ -69,3 +75,64 @@ def shard_chains(lengths, world: int, rank: int):
         owner[i] = r
         load[r] += int(lengths[i])
     return [i for i in range(len(lengths)) if owner[i] == rank]
+
+
+def neighbours(rank: int, world: int, periodic: bool):
+    """(left, right) neighbour ranks of `rank`'s part; None at a fixed end."""
+    left = (rank - 1) % world if (periodic or rank > 0) else None
+    right = (rank + 1) % world if (periodic or rank < world - 1) else None
+    return left, right
+
+
+def exchange_ghosts(ext, part: dict, ghost: int, left, right):
+    """Refresh the ghost zones of this rank's block `ext` ([ghost_left + sites + ghost_right, D],
+    a torch tensor on the backend's device; `part` as rk4_domain_part returns it) from the
+    neighbour ranks: the left ghosts become the left neighbour's last `ghost` sites, the right
+    ghosts the right neighbour's first `ghost` sites.  A neighbour equal to this rank (a single
+    periodic part) is copied locally."""
+    import torch.distributed as dist
+    gl, n = part["ghost_left"], part["sites"]
+    first = ext[gl:gl + ghost]
+    last = ext[gl + n - ghost:gl + n]
+    rank = dist.get_rank() if (dist.is_available() and dist.is_initialized()) else 0
+    reqs, recvs = [], []
+    # tag 0: sites travelling right (into a left ghost zone); tag 1: travelling left
+    if right is not None and right != rank:
+        reqs.append(dist.isend(last.contiguous(), right, tag=0))
+    if left is not None and left != rank:
+        reqs.append(dist.isend(first.contiguous(), left, tag=1))
+    if left is not None:
+        if left == rank:
+            ext[:gl].copy_(last)
+        else:
+            buf = ext.new_empty((gl,) + tuple(ext.shape[1:]))
+            reqs.append(dist.irecv(buf, left, tag=0))
+            recvs.append((buf, slice(0, gl)))
+    if right is not None:
+        if right == rank:
+            ext[gl + n:].copy_(first)
+        else:
+            buf = ext.new_empty((part["ghost_right"],) + tuple(ext.shape[1:]))
+            reqs.append(dist.irecv(buf, right, tag=1))
+            recvs.append((buf, slice(gl + n, gl + n + part["ghost_right"])))
+    for r in reqs:
+        r.wait()
+    for buf, sl in recvs:
+        ext[sl].copy_(buf)
+
+
+def integrate_decomposed(ext, comp, part: dict, ghost: int, reach: int, nsteps: int, integrate, left, right):
+    """Advance this rank's part nsteps steps: swap ghost zones, run `integrate(ext, comp, m)` for
+    m = min(floor(ghost / reach), steps left) steps on the part as a fixed-end chain, repeat.
+    On a GPU `integrate` is rk4_chain_integrate on a fixed-end handle of the block's length."""
+    period = ghost // reach if (left is not None or right is not None) else max(nsteps, 1)
+    if period < 1:
+        raise ValueError("ghost zones narrower than one step's reach")
+    done = 0
+    while done < nsteps:
+        m = min(period, nsteps - done)
+        exchange_ghosts(ext, part, ghost, left, right)
+        if comp is not None:
+            exchange_ghosts(comp, part, ghost, left, right)
+        integrate(ext, comp, m)
+        done += m
