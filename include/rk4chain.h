@@ -266,8 +266,10 @@ int rk4_fill_uniform(void *dst, int64_t count, uint64_t seed, uint64_t start, in
  * right ghost zone.  Every part has both ghost zones except the first (no left) and the last
  * (no right) part of a fixed-end chain.  comp (RK4_FP32_KAHAN) has the same layout.  Buffers
  * are caller-owned device memory, 16-byte aligned; ws 256-byte aligned.  Calls are
- * stream-ordered on the domain's stream unless they say they synchronise.  Ghost copies are
- * device-to-device cudaMemcpyAsync calls, one per ghost zone and array. */
+ * stream-ordered on the domain's stream unless they say they synchronise.  Inside
+ * rk4_domain_integrate and rk4_domain_energy an exchange is one gather-kernel launch over a
+ * table of the ghost zones kept in ws; rk4_domain_scatter and rk4_domain_exchange, which have
+ * no workspace, issue one device-to-device cudaMemcpyAsync per ghost zone and array. */
 typedef struct rk4_domain rk4_domain; /* opaque host-side handle */
 
 /* Creates a domain over one chain (model, precision, n, dt, bc, p, cuda_stream as for

@@ -36,8 +36,10 @@ struct rk4_domain {
   double dt = 0.01;
   std::vector<int64_t> site0, sites, row, gl, gr;  // per part
   cudaStream_t stream = nullptr;
-  double *h_out = nullptr;  // pinned: per-part energies
-  int *h_status = nullptr;  // pinned: status word read-back
+  std::vector<GhostPair> pairs;  // every ghost zone and the rows it is copied from
+  GhostPair *h_pairs = nullptr;   // pinned copy of `pairs`, uploaded to the workspace
+  double *h_out = nullptr;        // pinned: per-part energies
+  int *h_status = nullptr;        // pinned: status word read-back
 };
 
 namespace {
@@ -53,10 +55,10 @@ size_t batch_ws_bytes(const rk4_domain *d) {
   return align_up(b);
 }
 
-// Domain workspace: the batch handle's workspace, then a status header, the reduction partials
-// and one result per part.
+// Domain workspace: the batch handle's workspace, then a status header, the reduction partials,
+// one result per part and the ghost-zone table.
 struct DomLayout {
-  size_t batch, hdr, partials, result, total;
+  size_t batch, hdr, partials, result, pairs, total;
 };
 
 DomLayout dom_layout(const rk4_domain *d) {
@@ -65,7 +67,8 @@ DomLayout dom_layout(const rk4_domain *d) {
   L.hdr = L.batch;
   L.partials = L.hdr + align_up(sizeof(WsHeader));
   L.result = L.partials + align_up(sizeof(double) * kEnergyBlocks);
-  L.total = L.result + align_up(sizeof(double) * (size_t)d->nparts);
+  L.pairs = L.result + align_up(sizeof(double) * (size_t)d->nparts);
+  L.total = L.pairs + align_up(sizeof(GhostPair) * d->pairs.size());
   return L;
 }
 
@@ -86,30 +89,50 @@ cudaError_t copy_rows(const rk4_domain *d, void *dst, int64_t dst_row, const voi
                          cudaMemcpyDeviceToDevice, d->stream);
 }
 
-// Every ghost zone from the neighbouring part's interior: the left ghosts of part p are the
-// last `ghost` sites of part p - 1, its right ghosts the first `ghost` sites of part p + 1
-// (cyclically for periodic ends; a single periodic part is its own neighbour).
-cudaError_t exchange_one(const rk4_domain *d, void *buf) {
+// Every ghost zone and its source: the left ghosts of part p are the last `ghost` sites of part
+// p - 1, its right ghosts the first `ghost` sites of part p + 1 (cyclically for periodic ends;
+// a single periodic part is its own neighbour).
+void build_pairs(rk4_domain *d) {
   const int P = d->nparts;
   for (int p = 0; p < P; ++p) {
     if (d->gl[p]) {
       const int q = (p + P - 1) % P;
-      cudaError_t e = copy_rows(d, buf, d->row[p], buf, d->row[q] + d->gl[q] + d->sites[q] - d->ghost, d->ghost);
-      if (e != cudaSuccess) return e;
+      d->pairs.push_back({d->row[p], d->row[q] + d->gl[q] + d->sites[q] - d->ghost});
     }
     if (d->gr[p]) {
       const int r = (p + 1) % P;
-      cudaError_t e = copy_rows(d, buf, d->row[p] + d->gl[p] + d->sites[p], buf, d->row[r] + d->gl[r], d->ghost);
-      if (e != cudaSuccess) return e;
+      d->pairs.push_back({d->row[p] + d->gl[p] + d->sites[p], d->row[r] + d->gl[r]});
     }
+  }
+}
+
+// The exchange as plain device-to-device copies, one per zone and array (for the calls that
+// have no workspace to hold the zone table).
+cudaError_t exchange(const rk4_domain *d, void *state, void *comp) {
+  for (const GhostPair &z : d->pairs) {
+    cudaError_t e = copy_rows(d, state, z.dst_row, state, z.src_row, d->ghost);
+    if (e == cudaSuccess && comp) e = copy_rows(d, comp, z.dst_row, comp, z.src_row, d->ghost);
+    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-cudaError_t exchange(const rk4_domain *d, void *state, void *comp) {
-  cudaError_t e = exchange_one(d, state);
-  if (e == cudaSuccess && comp) e = exchange_one(d, comp);
-  return e;
+// The zone table into the workspace (once per call); then every exchange is one launch.  The
+// pinned staging copy is made on first use (creating a domain touches no CUDA API).
+cudaError_t upload_pairs(rk4_domain *d, char *ws, const DomLayout &L) {
+  if (d->pairs.empty()) return cudaSuccess;
+  if (!d->h_pairs) {
+    cudaError_t e = cudaMallocHost((void **)&d->h_pairs, sizeof(GhostPair) * d->pairs.size());
+    if (e != cudaSuccess) return e;
+    std::memcpy(d->h_pairs, d->pairs.data(), sizeof(GhostPair) * d->pairs.size());
+  }
+  return cudaMemcpyAsync(ws + L.pairs, d->h_pairs, sizeof(GhostPair) * d->pairs.size(), cudaMemcpyHostToDevice,
+                         d->stream);
+}
+
+cudaError_t exchange_kernel(const rk4_domain *d, void *state, void *comp, char *ws, const DomLayout &L) {
+  return launch_ghost_copy(state, comp, reinterpret_cast<const GhostPair *>(ws + L.pairs), (int)d->pairs.size(),
+                           d->ghost, d->D * (int)d->es, d->stream);
 }
 
 }  // namespace
@@ -163,6 +186,7 @@ int rk4_domain_create(rk4_domain **out, int model, int precision, int64_t n, dou
     return RK4_EINVAL;
   }
   d->rows = r0;
+  build_pairs(d);
   std::vector<int64_t> ext(nparts);
   std::vector<double> kap(nparts);
   std::vector<int8_t> bcs(nparts, (int8_t)RK4_FIXED);
@@ -261,9 +285,11 @@ int rk4_domain_integrate(rk4_domain *d, void *state, void *comp, void *ws, size_
   // steps between exchanges: the error front of the parts' fixed ends stays in the ghosts
   const int64_t period = any_ghost(d) ? d->ghost / ((int64_t)s * range) : std::max<int64_t>(nsteps, 1);
   if (period < 1) return RK4_EUNSUPPORTED;
+  char *w = static_cast<char *>(ws);
+  if (nsteps > 0 && upload_pairs(d, w, L) != cudaSuccess) return RK4_ECUDA;
   for (int64_t done = 0; done < nsteps;) {
     const int64_t m = std::min(period, nsteps - done);
-    if (any_ghost(d) && exchange(d, state, comp) != cudaSuccess) return RK4_ECUDA;
+    if (exchange_kernel(d, state, comp, w, L) != cudaSuccess) return RK4_ECUDA;
     const int rc = rk4_chain_integrate(d->h, state, comp, ws, L.batch, m, nullptr);
     if (rc != RK4_OK) return rc;
     done += m;
@@ -299,7 +325,8 @@ int rk4_domain_energy(rk4_domain *d, void *state, void *comp, void *ws, size_t w
   double *partials = reinterpret_cast<double *>(w + L.partials);
   double *res = reinterpret_cast<double *>(w + L.result);
   // bonds that cross a part boundary read the neighbour's site from the ghost zone
-  if (any_ghost(d) && exchange(d, state, comp) != cudaSuccess) return RK4_ECUDA;
+  if (upload_pairs(d, w, L) != cudaSuccess || exchange_kernel(d, state, comp, w, L) != cudaSuccess)
+    return RK4_ECUDA;
   if (cudaMemsetAsync(hdr, 0, sizeof(WsHeader), d->stream) != cudaSuccess) return RK4_ECUDA;
   for (int p = 0; p < d->nparts; ++p) {
     // part p as the fixed-end chain the kernels integrate; its interior is [gl, gl + sites)
@@ -328,6 +355,7 @@ int rk4_domain_status(rk4_domain *d, void *ws) {
 int rk4_domain_destroy(rk4_domain *d) {
   if (!d) return RK4_OK;
   rk4_chain_destroy(d->h);
+  if (d->h_pairs) cudaFreeHost(d->h_pairs);
   if (d->h_out) cudaFreeHost(d->h_out);
   if (d->h_status) cudaFreeHost(d->h_status);
   delete d;

@@ -120,6 +120,15 @@ cudaError_t launch_energy(int model, bool fp32, const void *state, const void *c
 cudaError_t launch_energy_range(int model, bool fp32, const void *state, const void *cmp, const ChainDesc &ch,
                                 int64_t lo, int64_t hi, const CoefD &cf, double *partials, double *out,
                                 WsHeader *hdr, cudaStream_t st);
+// One ghost zone of a sub-domain state: `ghost` rows starting at dst_row are copied from the
+// rows starting at src_row.
+struct GhostPair {
+  int64_t dst_row, src_row;
+};
+// Every zone of `pairs` (a device table) in one launch, for the state and, if not NULL, the
+// compensation; rows are row_bytes (a multiple of 4) long.
+cudaError_t launch_ghost_copy(void *state, void *comp, const GhostPair *pairs, int npairs, int64_t ghost,
+                              int row_bytes, cudaStream_t st);
 cudaError_t launch_fill_uniform(void *dst, int64_t count, uint64_t seed, uint64_t start, bool fp32,
                                 cudaStream_t st);
 cudaError_t launch_gen_staged_step(int model, bool fp32, int range, const GenStagedJob &job, const CoefD &cf,
