@@ -41,23 +41,41 @@ DT = 0.01
 SEED = 0x14120544
 D = 3
 HBM_GBS_FALLBACK = 6800.0
-# FP64 issue rates measured on this GPU model with independent dependency chains (8 per
-# thread, 4 blocks of 256 threads per SM): DFMA 0.5957e12/s, DADD and DMUL 0.5051e12/s; FP32
-# FMA 36.6e12/s.  The classical RK4 Roessler step issues 34 DFMA and 15 DADD per site-step
-# (4 x (4 FMA + 3 ADD) slope, 9 FMA stage states, 6 FMA + 3 ADD sum, 3 FMA update).  Every
-# addition can be issued as an exact FMA (a*1+b), so 49 instructions at the DFMA rate bound
-# the step; a variant built that way gave the same bits and the same time, so the slower DADD
-# rate is not the floor and the roof is the DFMA rate.
-FP64_DFMA_PEAK = 0.5957e12
-FP64_INST_PEAK = FP64_DFMA_PEAK
-FP32_INST_PEAK = 36.6e12
+# Arithmetic peaks for the ALU rooflines, measured by paper_1412_0544_gb300/pipe_probe.cu (run
+# by bench.py itself on rank 0 before the workload, so the denominator comes from the same GPU
+# and clocks; the constants below, from an earlier probe run on a GB300 at 2070 MHz, are the
+# fallback when the probe cannot run).  The classical RK4 Roessler step issues 34 DFMA and
+# 15 DADD per site-step (4 x (4 FMA + 3 ADD) slope, 9 FMA stage states, 6 FMA + 3 ADD sum,
+# 3 FMA update).  Every addition can be issued as an exact FMA (a*1+b), so 49 instructions at
+# the DFMA rate bound the step; a variant built that way gave the same bits and the same
+# time, so the slower DADD rate is not the floor and the roof is the DFMA rate.  FP32: the
+# larger of the scalar and packed (f32x2) FMA lane rates.
+FP64_INST_PEAK = 0.6272e12
+FP32_INST_PEAK = 40.12e12
+PEAK_SOURCE = "fallback constants from an earlier pipe_probe run"
+
+
+def probe_peaks():
+    """Measure the DFMA and FP32 FMA rates with the pipe probe; keep the constants on failure."""
+    global FP64_INST_PEAK, FP32_INST_PEAK, PEAK_SOURCE
+    try:
+        from paper_1412_0544_gb300 import pipe_probe
+        r = pipe_probe.run()
+        FP64_INST_PEAK = float(r["dfma_per_s"])
+        FP32_INST_PEAK = float(max(r["ffma_scalar_16chains_per_s"], r["ffma_packed_16lanes_per_s"]))
+        PEAK_SOURCE = "of measured: pipe_probe in this run"
+        return r
+    except Exception as e:  # the probe is a measurement aid; the bench still runs without it
+        return {"error": str(e)[:200]}
+
+
 FP64_INST_PER_SITE_STEP = 49     # 34 DFMA + 15 DADD
 FP32K_INST_PER_SITE_STEP = 61    # + 4 per component for the Kahan update
 # DRAM traffic (read + write bytes) per launch of the FP64 blocked kernel at N = 2^24 from one
 # ncu --set full capture, valid only for the kernel sources (hash) and the tiling recorded with
 # it; any other combination reports null.
-TRAFFIC = {("a2728451cc16c09e", "256,4,1"): 403167744 + 357529856,
-           ("a2728451cc16c09e", "256,4,2"): 402814976 + 357812224}
+TRAFFIC = {("e48b95e2bfea866c", "256,4,1"): 402773760 + 357229056,
+           ("e48b95e2bfea866c", "256,4,2"): 402781952 + 356905472}
 
 
 def kernel_hash() -> str:
@@ -538,6 +556,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP32 and batch side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-probe", action="store_true",
+                    help="quote ALU rooflines against the stored peaks instead of running pipe_probe first")
     ap.add_argument("--tiling", default=None, help="block,v,k of the FP64 kernel instead of the autotuner's pick")
     ap.add_argument("--sweep", action="store_true", help="site-steps/s against chain length instead of the bench line")
     ap.add_argument("--sweep-min", type=int, default=10, help="log2 of the smallest N of --sweep")
@@ -561,6 +581,7 @@ def main():
     stream = torch.cuda.current_stream()
     peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", HBM_GBS_FALLBACK))
+    probe = probe_peaks() if rank == 0 and not args.no_probe else None
 
     # --- the workload: one chain per rank (independent replicas, weak scaling) -------
     n = N_SITES
@@ -612,8 +633,8 @@ def main():
                 "traffic": traffic, "kernel": "k_blocked<double, Roessler>",
                 "per_unit": "49 FP64 instructions per interior site-step",
                 "launch_ms": launch_s * 1e3,
-                "peak_source": "of measured: DFMA issue rate (0.596e12/s); all 49 operations of the step "
-                               "can issue as DFMA",
+                "peak_source": PEAK_SOURCE + " (DFMA issue rate; all 49 operations of the step can issue "
+                                             "as DFMA)",
                 "hbm_frac_effective_state": sps_k * 2 * D * 8 / 1e9 / hbm_peak}
 
     # --- end to end through the C ABI with host buffers ------------------------------
@@ -669,6 +690,8 @@ def main():
             "e2e": e2e,
             "gpu_launches": args.steps * (plan_launches + 2),
             "kernel_hash": khash,
+            "alu_peaks": {"fp64_dfma_per_s": FP64_INST_PEAK, "fp32_fma_lanes_per_s": FP32_INST_PEAK,
+                          "source": PEAK_SOURCE, "probe": probe},
         }
         out.update(extras)
         if world == 1 and not args.no_cpu_baseline:

@@ -93,6 +93,100 @@ __device__ __forceinline__ void stage_update(int j, const R *k, R *y, R *u, R *a
   }
 }
 
+// ---- Packed FP32: two sites per instruction --------------------------------------------
+// GB300 issues FP32 add, multiply and FMA on register pairs (f32x2): one instruction performs
+// the same round-to-nearest operation on both halves, at the FMA pipe's per-lane rate, with
+// half the issue slots.  The FP32 kernels are issue-bound, so the tile kernels advance two
+// adjacent sites (the .x and .y halves) with these forms.  Each half gets exactly the
+// operation the scalar functions above perform, and negation flips the sign bits (exact,
+// signed zeros included), so packed and scalar kernels stay bit-identical.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 neg2(float2 a) {
+  return make_float2(__uint_as_float(__float_as_uint(a.x) ^ 0x80000000u),
+                     __uint_as_float(__float_as_uint(a.y) ^ 0x80000000u));
+}
+__device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
+
+// The coefficients as pairs: both halves from one chain, or from two sites (heterogeneous).
+struct Coef2 {
+  float2 a, b, c, kappa, w2, h2, h1, dt6;
+};
+__device__ __forceinline__ Coef2 pair_coef(const Coef<float> &p, const Coef<float> &q) {
+  return {make_float2(p.a, q.a),         make_float2(p.b, q.b),   make_float2(p.c, q.c),
+          make_float2(p.kappa, q.kappa), make_float2(p.w2, q.w2), make_float2(p.h2, q.h2),
+          make_float2(p.h1, q.h1),       make_float2(p.dt6, q.dt6)};
+}
+
+// slope() on two sites.
+template <int MODEL>
+__device__ __forceinline__ void slope2(const float2 *u, float2 xl, float2 xr, const Coef2 &cf, float2 *k) {
+  const float2 lap = fma2(splat(-2.f), u[0], add2(xl, xr));
+  if constexpr (MODEL == ROESSLER) {
+    k[0] = fma2(cf.kappa, lap, neg2(add2(u[1], u[2])));
+    k[1] = fma2(cf.a, u[1], u[0]);
+    k[2] = fma2(u[2], sub2(u[0], cf.c), cf.b);
+  } else {
+    k[0] = u[1];
+    k[1] = fma2(cf.kappa, lap, neg2(mul2(cf.w2, u[0])));
+  }
+}
+
+// stage_update() on two sites (FP32 with the Kahan update).
+template <int D>
+__device__ __forceinline__ void stage_update2(int j, const float2 *k, float2 *y, float2 *u, float2 *acc, float2 *cmp,
+                                              const Coef2 &cf) {
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    if (j == 0) {
+      acc[d] = k[d];
+      u[d] = fma2(cf.h2, k[d], y[d]);
+    } else if (j == 1) {
+      acc[d] = fma2(splat(2.f), k[d], acc[d]);
+      u[d] = fma2(cf.h2, k[d], y[d]);
+    } else if (j == 2) {
+      acc[d] = fma2(splat(2.f), k[d], acc[d]);
+      u[d] = fma2(cf.h1, k[d], y[d]);
+    } else {
+      const float2 s4 = add2(acc[d], k[d]);
+      const float2 s = fma2(cf.dt6, s4, neg2(cmp[d]));
+      const float2 t = add2(y[d], s);
+      cmp[d] = sub2(sub2(t, y[d]), s);
+      y[d] = t;
+    }
+  }
+}
+
 // Coefficients of one site of a heterogeneous chain: the chain's coefficients with the
 // site's own parameters p[0..P-1] substituted.
 template <typename R, int MODEL>
