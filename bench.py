@@ -74,8 +74,8 @@ FP32K_INST_PER_SITE_STEP = 61    # + 4 per component for the Kahan update
 # DRAM traffic (read + write bytes) per launch of the FP64 blocked kernel at N = 2^24 from one
 # ncu --set full capture, valid only for the kernel sources (hash) and the tiling recorded with
 # it; any other combination reports null.
-TRAFFIC = {("e48b95e2bfea866c", "256,4,1"): 402773760 + 357229056,
-           ("e48b95e2bfea866c", "256,4,2"): 402781952 + 356905472}
+TRAFFIC = {("b134305f0c50d378", "256,4,1"): 402880256 + 356902144,
+           ("b134305f0c50d378", "256,4,2"): 404093184 + 357194752}
 
 
 def kernel_hash() -> str:
@@ -146,6 +146,22 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(mhz)}
+
+
+def host_info() -> dict:
+    """The host the CPU baselines ran on: logical core count, architecture, CPU model."""
+    import platform
+    import subprocess
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu_model": model}
 
 
 def cpu_baseline(sample_sites: int = 1 << 22, sample_steps: int = 10) -> dict:
@@ -696,6 +712,7 @@ def main():
         out.update(extras)
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
+            out["cpu_baseline"]["host"] = host_info()
             if "paper_workload_2e20_fp64" in out:
                 out["paper_workload_2e20_fp64"]["oracle_1core"] = paper_workload_oracle()
         print(json.dumps(out))

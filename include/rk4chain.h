@@ -36,10 +36,14 @@
  *   - ws / ws_bytes: a device workspace of at least rk4_chain_workspace_bytes() bytes,
  *     256-byte aligned; contents need not be preserved between calls.  It holds the
  *     ping-pong copy of the state, reduction partials and the device status word.
- *   - Device-side errors (non-finite values seen by a reduction, a barrier wait that ran
- *     out of time) are latched in the status word inside ws and reported by
- *     rk4_chain_status().  Every integrate and energy call clears the status word when it
- *     starts, so the status describes the most recent such call on that workspace.
+ *   - Device-side errors (a NaN or infinity in a state that an integration stores or a
+ *     reduction reads, a barrier wait that ran out of time, in a debug build an index out of
+ *     range) are latched in the status word inside ws and reported by rk4_chain_status().
+ *     Every integrate and energy call clears the status word when it starts, so the status
+ *     describes the most recent such call on that workspace.
+ *   - Debug build: librk4chain_debug.so (build.py --debug-bounds) checks every global memory
+ *     range a kernel reads or writes against the buffer extents; an out-of-range access is
+ *     skipped and latches RK4_EBOUNDS.  Same ABI and results; slower.
  */
 #ifndef RK4CHAIN_H
 #define RK4CHAIN_H
@@ -58,6 +62,8 @@ extern "C" {
 #define RK4_ENONFINITE (-4)    /* a NaN or infinity was found in the state */
 #define RK4_ETIMEOUT (-5)      /* a bounded device-side wait gave up */
 #define RK4_EUNSUPPORTED (-6)  /* valid request this build does not support */
+#define RK4_EBOUNDS (-7)       /* debug build only: an index check caught an out-of-range access
+                                  (the access was skipped); see the build notes below */
 
 enum rk4_model { RK4_ROESSLER = 0, RK4_HARMONIC = 1 };
 enum rk4_precision { RK4_FP64 = 0, RK4_FP32_KAHAN = 1 };
@@ -208,7 +214,9 @@ int rk4_chain_energy(rk4_chain *h, const void *state, const void *comp, void *ws
 int rk4_chain_energy_static(rk4_chain *h, const void *state, const void *comp, double *out);
 
 /* Synchronises the stream, reads and clears the device status word in ws, and returns the
- * first latched error (RK4_ENONFINITE, RK4_ETIMEOUT) or RK4_OK. */
+ * latched error (RK4_ETIMEOUT, else RK4_EBOUNDS, else RK4_ENONFINITE) or RK4_OK.  An
+ * integration that stored a NaN or infinity (an unstable dt, a blow-up) reports
+ * RK4_ENONFINITE here. */
 int rk4_chain_status(rk4_chain *h, void *ws);
 
 /* Options (enum rk4_option): RK4_OPT_GRAPHS (1 = replay launch sequences from a cached CUDA

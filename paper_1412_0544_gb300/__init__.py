@@ -16,10 +16,13 @@ import re
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "librk4chain.so")
+# RK4CHAIN_LIBRARY selects another build of the same ABI (for example librk4chain_debug.so,
+# whose kernels check every memory range they touch).
+LIB_PATH = os.environ.get("RK4CHAIN_LIBRARY") or os.path.join(_HERE, "librk4chain.so")
 HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "rk4chain.h")
 
 RK4_OK, RK4_EINVAL, RK4_ENOMEM_WS, RK4_ECUDA, RK4_ENONFINITE, RK4_ETIMEOUT, RK4_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+RK4_EBOUNDS = -7
 RK4_ROESSLER, RK4_HARMONIC = 0, 1
 RK4_FP64, RK4_FP32_KAHAN = 0, 1
 RK4_PERIODIC, RK4_FIXED = 0, 1

@@ -4,6 +4,11 @@ Translation units compile in parallel; the shared library links the CUDA runtime
 so the only runtime dependency is the NVIDIA driver.  Run ``python
 paper_1412_0544_gb300/build.py`` (it does not import the package, whose import needs the
 built library) or ``__graft_entry__.build()``.
+
+``--debug-bounds`` builds librk4chain_debug.so instead: the same sources with
+-DRK4_DEBUG_BOUNDS, whose kernels check every global memory range against the buffer
+extents and latch RK4_EBOUNDS instead of making an out-of-range access (the sanitizer
+substitute; select it with the RK4CHAIN_LIBRARY environment variable).
 """
 from __future__ import annotations
 
@@ -17,6 +22,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librk4chain.so")
+LIB_DEBUG = os.path.join(HERE, "librk4chain_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -38,16 +44,20 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> str:
+def build(force: bool = False, verbose_ptxas: bool = False, debug_bounds: bool = False) -> str:
     """Compile and link; returns the library path.  Skips work when up to date."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
-        return LIB
-    os.makedirs(OBJ, exist_ok=True)
+    lib = LIB_DEBUG if debug_bounds else LIB
+    obj_dir = OBJ + ("_debug" if debug_bounds else "")
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps_mtime():
+        return lib
+    os.makedirs(obj_dir, exist_ok=True)
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+    if debug_bounds:
+        extra += ["-DRK4_DEBUG_BOUNDS"]
 
     def compile_one(src):
-        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -60,14 +70,15 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     if verbose_ptxas:
         for _, log in results:
             sys.stderr.write(log)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *[o for o, _ in results]]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv,
+                debug_bounds="--debug-bounds" in sys.argv))

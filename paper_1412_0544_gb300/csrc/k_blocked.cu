@@ -24,7 +24,8 @@ __global__ void __launch_bounds__(max_threads_for(V)) k_blocked(BlockedJob job, 
   }
   tile_item<R, MODEL, V, KAHAN, false, HET>(static_cast<const R *>(job.in), static_cast<R *>(job.out),
                                             static_cast<const R *>(job.cin), static_cast<R *>(job.cout), ch, tile,
-                                            job.K, job.G, c, smem, static_cast<const R *>(job.sp));
+                                            job.K, job.G, c, smem, job.total, job.hdr,
+                                            static_cast<const R *>(job.sp));
 }
 
 size_t blocked_smem_bytes(int model, bool fp32, int v, int block, bool het) {

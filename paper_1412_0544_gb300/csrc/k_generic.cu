@@ -68,8 +68,9 @@ __global__ void __launch_bounds__(256) k_gen_slope(GenStagedJob job, Coef<R> cf,
     }
     const int64_t li = i - ch.off;
     auto xat = [&](int64_t q) -> R {  // coupling coordinate of chain site q (boundary-resolved)
-      if (ch.bc == PERIODIC) return src[(ch.off + wrap(q, ch.n)) * D];
-      return (q < 0 || q >= ch.n) ? R(0) : src[(ch.off + q) * D];
+      const int64_t g = (ch.bc == PERIODIC) ? ch.off + wrap(q, ch.n) : ((q < 0 || q >= ch.n) ? -1 : ch.off + q);
+      if (g < 0 || !bounds_ok(job.hdr, in_range(g, 1, job.total))) return R(0);
+      return src[g * D];
     };
     R u[D], k[D];
 #pragma unroll
@@ -100,11 +101,14 @@ __global__ void __launch_bounds__(256) k_gen_combine(GenStagedJob job, Tableau<R
 #pragma unroll
       for (int d = 0; d < D; ++d) k[m][d] = (m < tb.s) ? K[m * plane + i * D + d] : R(0);
     gen_combine<R, D, KAHAN>(tb, k, y, cmp);
+    bool bad = false;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       Y[i * D + d] = y[d];
       if constexpr (KAHAN) CMP[i * D + d] = cmp[d];
+      bad |= nonfinite(y[d]);
     }
+    if (bad && job.hdr) atomicOr(&job.hdr->status, ST_NONFINITE);
   }
 }
 
@@ -202,8 +206,9 @@ __global__ void __launch_bounds__(gen_max_threads(V)) k_gen_blocked(BlockedJob j
   }
   const int G = job.G;
   const int64_t t0 = tile * (int64_t)G - H;
-  tile_load<R, D, false>(tl, static_cast<const R *>(job.in), ch.off, ch.n, ch.bc, t0, W);
-  if constexpr (KAHAN) tile_load<R, D, false>(ctl, static_cast<const R *>(job.cin), ch.off, ch.n, ch.bc, t0, W);
+  tile_load<R, D, false>(tl, static_cast<const R *>(job.in), ch.off, ch.n, ch.bc, t0, W, job.total, job.hdr);
+  if constexpr (KAHAN)
+    tile_load<R, D, false>(ctl, static_cast<const R *>(job.cin), ch.off, ch.n, ch.bc, t0, W, job.total, job.hdr);
   __syncthreads();
   R y[V][D], cmp[V][D];
   const int base = threadIdx.x * V;
@@ -226,20 +231,24 @@ __global__ void __launch_bounds__(gen_max_threads(V)) k_gen_blocked(BlockedJob j
   } else {
     gen_tile_advance<R, MODEL, V, RANGE, KAHAN, false>(y, cmp, 0u, job.K, c, kappa2, tb, edge);
   }
+  const int64_t g0 = t0 + H;
+  const int64_t rem = ch.n - g0;
+  const int cnt = (int)(rem < G ? rem : G);
+  bool bad = false;  // a stored (interior) value is NaN or infinite
 #pragma unroll
-  for (int v = 0; v < V; ++v)
+  for (int v = 0; v < V; ++v) {
+    const bool stored = base + v >= H && base + v < H + cnt;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       tl[(base + v) * D + d] = y[v][d];
       if constexpr (KAHAN) ctl[(base + v) * D + d] = cmp[v][d];
+      bad |= stored && nonfinite(y[v][d]);
     }
-  __syncthreads();
-  const int64_t g0 = t0 + H;
-  const int64_t rem = ch.n - g0;
-  const int cnt = (int)(rem < G ? rem : G);
+  }
+  report_nonfinite(job.hdr, __syncthreads_or(bad));
   if (cnt > 0) {
-    tile_store<R, D>(static_cast<R *>(job.out), tl, ch.off, H, g0, cnt);
-    if constexpr (KAHAN) tile_store<R, D>(static_cast<R *>(job.cout), ctl, ch.off, H, g0, cnt);
+    tile_store<R, D>(static_cast<R *>(job.out), tl, ch.off, H, g0, cnt, job.total, W, job.hdr);
+    if constexpr (KAHAN) tile_store<R, D>(static_cast<R *>(job.cout), ctl, ch.off, H, g0, cnt, job.total, W, job.hdr);
   }
 }
 

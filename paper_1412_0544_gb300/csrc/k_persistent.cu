@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(max_threads_for(V), (V >= 8 && KAHAN) ? 2 : 1)
         tile = item - prefix[ci];
         c.kappa = (R)ch.kappa;
       }
-      tile_item<R, MODEL, V, KAHAN, true>(in, out, cin, cout, ch, tile, K, G, c, smem);
+      tile_item<R, MODEL, V, KAHAN, true>(in, out, cin, cout, ch, tile, K, G, c, smem, job.total, job.hdr);
       // tile_item ends with a barrier, so every thread has read s_item before it is rewritten
       if (threadIdx.x == 0) s_item = (long long)atomicAdd(ctr, 1ull);
       __syncthreads();

@@ -42,9 +42,11 @@ __global__ void __launch_bounds__(256) k_staged(StagedJob job, Coef<R> cf, int j
     if (ch.bc == PERIODIC) {
       const int64_t il = (li == 0) ? ch.n - 1 : li - 1;
       const int64_t ir = (li == ch.n - 1) ? 0 : li + 1;
+      if (!bounds_ok(job.hdr, in_range(ch.off + il, 1, job.total) && in_range(ch.off + ir, 1, job.total))) continue;
       xl = src[(ch.off + il) * D];
       xr = src[(ch.off + ir) * D];
     } else {
+      if (!bounds_ok(job.hdr, in_range(li, 1, ch.n))) continue;
       xl = (li == 0) ? R(0) : src[(i - 1) * D];
       xr = (li == ch.n - 1) ? R(0) : src[(i + 1) * D];
     }
@@ -57,11 +59,14 @@ __global__ void __launch_bounds__(256) k_staged(StagedJob job, Coef<R> cf, int j
         ACC[i * D + d] = acc[d];
       }
     } else {
+      bool bad = false;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         Y[i * D + d] = y[d];
         if constexpr (KAHAN) CMP[i * D + d] = cmp[d];
+        bad |= nonfinite(y[d]);
       }
+      if (bad && job.hdr) atomicOr(&job.hdr->status, ST_NONFINITE);
     }
   }
 }

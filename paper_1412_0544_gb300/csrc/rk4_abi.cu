@@ -329,6 +329,7 @@ cudaError_t enqueue_integrate(rk4_chain *h, int kernel, void *state, void *comp,
     j.one = h->chains[0];
     j.chains = dev_chains(h, ws, L);
     j.total = h->total;
+    j.hdr = reinterpret_cast<WsHeader *>(ws + L.hdr);
     for (int64_t s = 0; s < nsteps; ++s) {
       e = launch_gen_staged_step(h->model, h->fp32, coupling_range(h), j, cf, h->tab, h->dt, st);
       if (e != cudaSuccess) return e;
@@ -344,6 +345,7 @@ cudaError_t enqueue_integrate(rk4_chain *h, int kernel, void *state, void *comp,
     j.one = h->chains[0];
     j.chains = dev_chains(h, ws, L);
     j.total = h->total;
+    j.hdr = reinterpret_cast<WsHeader *>(ws + L.hdr);
     j.acc = ws + L.acc;
     void *u0 = ws + L.u0, *u1 = ws + L.u1;
     for (int64_t s = 0; s < nsteps; ++s) {
@@ -365,6 +367,8 @@ cudaError_t enqueue_integrate(rk4_chain *h, int kernel, void *state, void *comp,
     j.one = h->chains[0];
     j.chains = dev_chains(h, ws, L);
     j.sp = h->site_params;
+    j.hdr = reinterpret_cast<WsHeader *>(ws + L.hdr);
+    j.total = h->total;
     const int32_t *pre = h->nchains > 1 ? reinterpret_cast<const int32_t *>(ws + L.prefix) : nullptr;
     for (int64_t i = 0; i < P.count(); ++i) {
       const int k = P.k_at(i);
@@ -408,6 +412,7 @@ cudaError_t enqueue_integrate(rk4_chain *h, int kernel, void *state, void *comp,
     j.ntail = (int)P.tail.size();
     for (int i = 0; i < j.ntail; ++i) j.tail[i] = P.tail[i];
     j.hdr = reinterpret_cast<WsHeader *>(ws + L.hdr);
+    j.total = h->total;
     // A barrier waits at most one time block; unless the caller set the bound, allow 20x a
     // pessimistic estimate of one (1e9 site-steps/s) so that very large batches cannot time
     // out spuriously.
@@ -746,6 +751,7 @@ int rk4_chain_status(rk4_chain *h, void *ws) {
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return RK4_ECUDA;
   const int s = *h->h_status;
   if (s & ST_TIMEOUT) return RK4_ETIMEOUT;
+  if (s & ST_BOUNDS) return RK4_EBOUNDS;
   if (s & ST_NONFINITE) return RK4_ENONFINITE;
   return RK4_OK;
 }
@@ -796,6 +802,7 @@ int rk4_debug_barrier_timeout(rk4_chain *h, void *state, void *comp, void *ws, s
   j.nmain = 1;
   j.ntail = 0;
   j.hdr = reinterpret_cast<WsHeader *>(w + L.hdr);
+  j.total = h->total;
   j.timeout_ns = timeout_ns;
   j.extra_arrivals = 1;
   int grid = persistent_max_grid(h->model, h->fp32, h->tiling.v, h->tiling.block);
@@ -974,6 +981,7 @@ const char *rk4_strerror(int code) {
     case RK4_ENONFINITE: return "non-finite value in the state";
     case RK4_ETIMEOUT: return "device-side wait timed out";
     case RK4_EUNSUPPORTED: return "unsupported request";
+    case RK4_EBOUNDS: return "an index check of the debug build caught an out-of-range access";
     default: return "unknown error";
   }
 }

@@ -30,8 +30,9 @@ struct TableauD {
   double b[kMaxStages];
 };
 
-// Device status word bits (in the workspace header).
-enum : int { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
+// Device status word bits (in the workspace header).  ST_BOUNDS is only ever set by a library
+// built with -DRK4_DEBUG_BOUNDS (index checks on every global access; see rk4_tile.cuh).
+enum : int { ST_NONFINITE = 1, ST_TIMEOUT = 2, ST_BOUNDS = 4 };
 
 // Workspace header: status word, grid-barrier counters.  256 bytes.
 struct WsHeader {
@@ -57,6 +58,8 @@ struct BlockedJob {
   int G;                        // interior sites per tile
   int64_t ntiles;               // tiles in the launch
   const void *sp;               // per-site parameters of a heterogeneous chain, or NULL
+  WsHeader *hdr;                // status word (non-finite results, debug bounds checks)
+  int64_t total;                // sites in the state buffers
 };
 
 struct StagedJob {
@@ -70,6 +73,7 @@ struct StagedJob {
   const ChainDesc *chains;   // device table for batches (site -> chain by binary search)
   int64_t total;             // total sites
   const void *sp;            // per-site parameters of a heterogeneous chain, or NULL
+  WsHeader *hdr;             // status word
 };
 
 // One step of the generic standard scheme: stage states, slopes and the combination, each a
@@ -83,6 +87,7 @@ struct GenStagedJob {
   ChainDesc one;
   const ChainDesc *chains;
   int64_t total;
+  WsHeader *hdr;  // status word
 };
 
 struct PersistentJob {
@@ -102,6 +107,7 @@ struct PersistentJob {
   WsHeader *hdr;                // status word and barrier counters (zeroed before launch)
   long long timeout_ns;         // bound on any single barrier wait
   int extra_arrivals;           // test hook: barrier waits for this many blocks that never come
+  int64_t total;                // sites in the state buffers
 };
 
 // Launchers (return a cudaError_t).  R is selected by `fp32` (FP32 + Kahan) or double.

@@ -22,6 +22,40 @@ namespace rk4d {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Index checks of a debug build (-DRK4_DEBUG_BOUNDS): a range that would leave its buffer
+// latches ST_BOUNDS in the status word and the access is skipped.  In a release build the
+// check is the constant true and costs nothing.
+__device__ __forceinline__ bool bounds_ok(WsHeader *hdr, bool ok) {
+#ifdef RK4_DEBUG_BOUNDS
+  if (!ok && hdr) atomicOr(&hdr->status, ST_BOUNDS);
+  return ok;
+#else
+  (void)hdr;
+  (void)ok;
+  return true;
+#endif
+}
+
+// Whether [first, first + count) lies inside [0, size).
+__device__ __forceinline__ bool in_range(int64_t first, int64_t count, int64_t size) {
+  return first >= 0 && count >= 0 && first + count <= size;
+}
+
+// NaN or infinity, tested on the exponent bits with integer instructions: a floating-point
+// compare would take issue slots of the FP64 pipe, which bounds the FP64 kernels.
+__device__ __forceinline__ bool nonfinite(double x) {
+  return (__double2hiint(x) & 0x7ff00000) == 0x7ff00000;
+}
+__device__ __forceinline__ bool nonfinite(float x) {
+  return (__float_as_uint(x) & 0x7f800000u) == 0x7f800000u;
+}
+
+// Latch ST_NONFINITE when any value of a result about to be stored is NaN or infinite (one
+// thread per block reports; `any` is the block-wide vote).
+__device__ __forceinline__ void report_nonfinite(WsHeader *hdr, int any) {
+  if (any && threadIdx.x == 0 && hdr) atomicOr(&hdr->status, ST_NONFINITE);
+}
+
 // Largest block the tile kernels are compiled for, by sites per thread: the register budget
 // (about 9 values per site plus temporaries) must fit 65536 registers per block.
 __host__ __device__ constexpr int max_threads_for(int v) { return v <= 1 ? 1024 : (v <= 4 ? 512 : 256); }
@@ -140,9 +174,10 @@ template <bool COH, typename T> __device__ __forceinline__ T gld(const T *p) {
 // for shorter periodic chains.
 template <typename R, int D, bool COH>
 __device__ __forceinline__ void tile_load(R *tile, const R *__restrict__ src, int64_t off, int64_t n, int bc,
-                                          int64_t t0, int W) {
+                                          int64_t t0, int W, int64_t sites, WsHeader *hdr) {
   const int total = W * D;
   if (t0 >= 0 && t0 + W <= n) {
+    if (!bounds_ok(hdr, in_range(off + t0, W, sites))) return;
     const R *s = src + (off + t0) * D;
     if ((reinterpret_cast<uintptr_t>(s) & 15u) == 0 && ((total * (int)sizeof(R)) & 15) == 0) {
       const int nv = total * (int)sizeof(R) / 16;
@@ -174,6 +209,7 @@ __device__ __forceinline__ void tile_load(R *tile, const R *__restrict__ src, in
     }
     R *dst = tile + covered * D;
     const int cnt = len * D;
+    if (seg && !bounds_ok(hdr, in_range(seg - src, cnt, sites * D))) seg = nullptr;
     if (seg) {
       for (int e = threadIdx.x; e < cnt; e += blockDim.x) dst[e] = gld<COH>(seg + e);
     } else {
@@ -186,7 +222,8 @@ __device__ __forceinline__ void tile_load(R *tile, const R *__restrict__ src, in
 // Store `cnt` sites of the tile starting at tile-local site `first` to chain index g0.
 template <typename R, int D>
 __device__ __forceinline__ void tile_store(R *__restrict__ dst, const R *tile, int64_t off, int first, int64_t g0,
-                                           int cnt) {
+                                           int cnt, int64_t sites, int W, WsHeader *hdr) {
+  if (!bounds_ok(hdr, in_range(off + g0, cnt, sites) && in_range(first, cnt, W))) return;
   const int total = cnt * D;
   R *d0 = dst + (off + g0) * D;
   const R *s0 = tile + first * D;
@@ -203,10 +240,13 @@ __device__ __forceinline__ void tile_store(R *__restrict__ dst, const R *tile, i
 
 // Process one (chain, tile) item end to end: load, advance K steps, store the interior.
 // Shared memory: edge[128] | tile[W*D] | ctile[W*D] (Kahan) | ptile[W*P] (heterogeneous).
+// `sites` is the number of sites in the state buffers (for the debug bounds checks); hdr the
+// status word, where a non-finite stored value is reported.
 template <typename R, int MODEL, int V, bool KAHAN, bool COH, bool HET = false>
 __device__ __forceinline__ void tile_item(const R *__restrict__ in, R *__restrict__ out, const R *__restrict__ cin,
                                           R *__restrict__ cout, const ChainDesc &ch, int64_t tile, int K, int G,
-                                          const Coef<R> &cf, unsigned char *smem, const R *__restrict__ sp = nullptr) {
+                                          const Coef<R> &cf, unsigned char *smem, int64_t sites, WsHeader *hdr,
+                                          const R *__restrict__ sp = nullptr) {
   constexpr int D = Dim<MODEL>::D;
   constexpr int P = Dim<MODEL>::P;
   R *edge = reinterpret_cast<R *>(smem);
@@ -217,9 +257,9 @@ __device__ __forceinline__ void tile_item(const R *__restrict__ in, R *__restric
   const int H = 4 * K;
   const int64_t t0 = tile * (int64_t)G - H;
 
-  tile_load<R, D, COH>(tl, in, ch.off, ch.n, ch.bc, t0, W);
-  if constexpr (KAHAN) tile_load<R, D, COH>(ctl, cin, ch.off, ch.n, ch.bc, t0, W);
-  if constexpr (HET) tile_load<R, P, COH>(ptl, sp, ch.off, ch.n, ch.bc, t0, W);
+  tile_load<R, D, COH>(tl, in, ch.off, ch.n, ch.bc, t0, W, sites, hdr);
+  if constexpr (KAHAN) tile_load<R, D, COH>(ctl, cin, ch.off, ch.n, ch.bc, t0, W, sites, hdr);
+  if constexpr (HET) tile_load<R, P, COH>(ptl, sp, ch.off, ch.n, ch.bc, t0, W, sites, hdr);
   __syncthreads();
 
   R y[V][D], cmp[V][D];
@@ -251,20 +291,24 @@ __device__ __forceinline__ void tile_item(const R *__restrict__ in, R *__restric
     tile_advance<R, MODEL, V, KAHAN, false, HET>(y, cmp, 0u, K, cf, edge, cs);
   }
 
+  const int64_t g0 = t0 + H;  // = tile * G
+  const int64_t rem = ch.n - g0;
+  const int cnt = (int)(rem < G ? rem : G);
+  bool bad = false;  // a stored (interior) value is NaN or infinite
 #pragma unroll
-  for (int v = 0; v < V; ++v)
+  for (int v = 0; v < V; ++v) {
+    const bool stored = base + v >= H && base + v < H + cnt;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       tl[(base + v) * D + d] = y[v][d];
       if constexpr (KAHAN) ctl[(base + v) * D + d] = cmp[v][d];
+      bad |= stored && nonfinite(y[v][d]);
     }
-  __syncthreads();
-  const int64_t g0 = t0 + H;  // = tile * G
-  const int64_t rem = ch.n - g0;
-  const int cnt = (int)(rem < G ? rem : G);
+  }
+  report_nonfinite(hdr, __syncthreads_or(bad));
   if (cnt > 0) {
-    tile_store<R, D>(out, tl, ch.off, H, g0, cnt);
-    if constexpr (KAHAN) tile_store<R, D>(cout, ctl, ch.off, H, g0, cnt);
+    tile_store<R, D>(out, tl, ch.off, H, g0, cnt, sites, W, hdr);
+    if constexpr (KAHAN) tile_store<R, D>(cout, ctl, ch.off, H, g0, cnt, sites, W, hdr);
   }
   __syncthreads();  // shared memory is reused by the next item
 }
