@@ -8,7 +8,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import (RK4_FP32_KAHAN, RK4_FP64, RK4_KERNEL_AUTO, RK4_PERIODIC, RK4_ROESSLER, rk4_batch_create,
-               rk4_chain_autotune, rk4_chain_create, rk4_chain_destroy, rk4_chain_energy, rk4_chain_get_tiling,
+               rk4_chain_create, rk4_chain_destroy, rk4_chain_energy, rk4_chain_get_tiling,
                rk4_chain_integrate, rk4_chain_set_kernel, rk4_chain_set_tiling, rk4_chain_shape,
                rk4_chain_status, rk4_chain_workspace_bytes)
 
@@ -80,11 +80,17 @@ class Chain:
     def status(self) -> int:
         return rk4_chain_status(self.h, self.workspace())
 
-    def autotune(self, state, comp, probe_steps: int = 16) -> dict:
-        """Tunes on copies of state/comp (the tuner advances the buffers it is given)."""
+    def autotune(self, state, comp, probe_steps: int = 16, *, cache: str | None = None, scheme: str = "rk4") -> dict:
+        """Tunes on copies of state/comp (the tuner advances the buffers it is given).  With a
+        cache file (``cache`` or RK4CHAIN_TUNE_CACHE) a stored choice for the same GPU and
+        workload is applied instead of tuning (tune_cache); ``scheme`` tags the workload when a
+        tableau, second-neighbour coupling or site parameters were set on the handle."""
+        from . import tune_cache
         s = state.clone()
         c = comp.clone() if comp is not None else None
-        return rk4_chain_autotune(self.h, s, c, self.workspace(), probe_steps)
+        key = tune_cache.make_key(self._torch.cuda.get_device_name(), self.model, self.precision, self.nchains,
+                                  self.total, scheme)
+        return tune_cache.autotune(self.h, s, c, self.workspace(), key, probe_steps=probe_steps, path=cache)
 
     def close(self):
         if self.h is not None:
