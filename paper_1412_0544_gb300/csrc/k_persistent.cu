@@ -50,7 +50,8 @@ __device__ __forceinline__ bool grid_barrier(WsHeader *hdr, long long timeout_ns
 }
 
 template <typename R, int MODEL, int V, bool KAHAN>
-__global__ void __launch_bounds__(max_threads_for(V), (V >= 8 && KAHAN) ? 2 : 1) k_persistent(PersistentJob job, Coef<R> cf) {
+__global__ void __launch_bounds__(max_threads_for(V), (V >= 2 && KAHAN) ? 2 : 1)  // FP32: two resident blocks
+    k_persistent(PersistentJob job, Coef<R> cf) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t nblocks_t = job.nmain + job.ntail;
   for (int64_t t = 0; t < nblocks_t; ++t) {
