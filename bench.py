@@ -386,6 +386,57 @@ def size_sweep(args):
     return 0
 
 
+def tiling_sweep(args):
+    """The cluster-size study (Sec. 3.2.1, the paper's granularity dependence) on the N = 2^24
+    periodic Roessler chain: for tile widths W = block x v from 256 to 8192 sites and k = 1, 2,
+    4, 8 steps per launch (G = W - 8k interior sites), the fastest (block, v) realising W, FP64
+    and FP32-Kahan.  Cells no block shape can realise (registers or shared memory per block)
+    are printed with "infeasible" and the reason.  One JSON object per cell."""
+    import torch
+    import paper_1412_0544_gb300 as rk
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n = N_SITES
+    for prec, pname in ((rk.RK4_FP64, "fp64"), (rk.RK4_FP32_KAHAN, "fp32_kahan")):
+        dtype = torch.float64 if prec == rk.RK4_FP64 else torch.float32
+        h = rk.rk4_chain_create(rk.RK4_ROESSLER, prec, n, DT, rk.RK4_PERIODIC, None, stream)
+        try:
+            rk.rk4_chain_set_kernel(h, rk.RK4_KERNEL_BLOCKED)
+            st = torch.empty((n, D), dtype=dtype, device="cuda")
+            rk.rk4_fill_uniform(st, n * D, SEED, 0, prec, stream)
+            cp = torch.zeros_like(st) if prec == rk.RK4_FP32_KAHAN else None
+            ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+            for W in (256, 512, 1024, 2048, 4096, 8192):
+                for k in (1, 2, 4, 8):
+                    best, tried, reasons = None, [], []
+                    for v in (1, 2, 4, 8):
+                        block = W // v
+                        if block < 64 or block > 1024 or block % 32:
+                            reasons.append(f"v={v}: block {block} outside 64..1024")
+                            continue
+                        try:
+                            rk.rk4_chain_set_tiling(h, block, v, k)
+                        except rk.RK4Error:
+                            reasons.append(f"v={v}: block {block} exceeds the kernel's limit (registers or shared memory)")
+                            continue
+                        nsteps = 16 * k if prec == rk.RK4_FP32_KAHAN else 8 * k
+                        rk.rk4_chain_integrate(h, st, cp, ws, nsteps)  # warm-up, graph capture
+                        el = min(time_integrate(rk, h, st, cp, ws, nsteps, 1, torch) for _ in range(2))
+                        sps = n * nsteps / el
+                        tried.append({"block": block, "v": v, "site_steps_per_s": sps})
+                        if best is None or sps > best["site_steps_per_s"]:
+                            best = tried[-1]
+                    line = {"precision": pname, "N": n, "W": W, "k": k, "G": W - 8 * k}
+                    if best is None:
+                        line.update({"infeasible": True, "reason": "; ".join(reasons)})
+                    else:
+                        line.update({"best": best, "tried": tried})
+                    print(json.dumps(line), flush=True)
+        finally:
+            rk.rk4_chain_destroy(h)
+    return 0
+
+
 # Dormand and Prince (1980) RK5(4)7M, fifth-order weights, used with a fixed step
 DOPRI5_A = np.array([
     [0, 0, 0, 0, 0, 0, 0],
@@ -583,6 +634,8 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="site-steps/s against chain length instead of the bench line")
     ap.add_argument("--sweep-min", type=int, default=10, help="log2 of the smallest N of --sweep")
     ap.add_argument("--sweep-max", type=int, default=27, help="log2 of the largest N of --sweep")
+    ap.add_argument("--tiling-sweep", action="store_true",
+                    help="site-steps/s against tile width and steps per launch instead of the bench line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -590,6 +643,8 @@ def main():
         return run_reference(args)
     if args.sweep:
         return size_sweep(args)
+    if args.tiling_sweep:
+        return tiling_sweep(args)
 
     import torch
 
