@@ -1,7 +1,7 @@
 """GPU parity: the CUDA kernels against the CPU oracle and against each other (needs a GB300).
 
 * FP64 results match the oracle within 1e-12 (max-abs error relative to max |oracle|) after
-  1000 steps -- the tolerance the spec workload states.
+  1000 steps -- the tolerance required of the FP64 path.
 * The blocked kernel (every tiling), the fused k = 1 kernel and the persistent kernel are bit
   for bit equal to the one-stage-per-launch kernel.
 * FP32-Kahan results are compared with the FP64 oracle started from the same FP32 values and
