@@ -730,7 +730,10 @@ def main():
     del host, dev2
 
     extras = {}
-    if not args.no_extras:
+    if world > 1:
+        # per-GPU side measurements add nothing to a weak-scaling line and would hold every GPU
+        extras["extras"] = "skipped for n_gpus > 1 (run with one GPU)"
+    elif not args.no_extras:
         extras["fixed_fp64_2e27"] = fixed_fp64_extra(rk, torch, stream)
         extras["fp32_kahan_2e27"] = fp32_kahan_extra(rk, torch, stream)
         extras["batch_fp64"] = batch_extra(rk, torch, stream, rk.RK4_FP64)
