@@ -56,6 +56,32 @@ __global__ void fp64_chain(double *out, int iters, double a, double b) {
   if (s == -12345.0) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// DFMA whose three operands are all per-chain registers that change every iteration (the form
+// of most DFMAs in the RK4 step), against the chains above, whose multiplier and addend are
+// loop-invariant.  Three coupled chains per group: x = x*y + z, y = y*z + x, z = z*x + y.
+template <int G>
+__global__ void fp64_3reg(double *out, int iters, double a, double b) {
+  double x[G], y[G], z[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    x[g] = 1.0 + 1e-9 * (threadIdx.x + g);
+    y[g] = a;
+    z[g] = b;
+  }
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      x[g] = __fma_rn(x[g], y[g], z[g]);
+      y[g] = __fma_rn(y[g], z[g], x[g]);
+      z[g] = __fma_rn(z[g], x[g], y[g]);
+    }
+  }
+  double s = 0;
+#pragma unroll
+  for (int g = 0; g < G; ++g) s += x[g] + y[g] + z[g];
+  if (s == -12345.0) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 template <int CH>
 __global__ void fp32_chain(double *out, int iters, double a, double b) {
   const float fa = (float)a, fb = (float)b;
@@ -141,6 +167,7 @@ int main() {
   const double dadd = rate(fp64_chain<1, 8>, sms, 4096, 8, out);
   const double dmul = rate(fp64_chain<2, 8>, sms, 4096, 8, out);
   const double dmix = rate(fp64_chain<3, 8>, sms, 2048, 24, out);
+  const double d3reg = rate(fp64_3reg<8>, sms, 2048, 24, out);
   const double ffma8 = rate(fp32_chain<8>, sms, 1 << 16, 8, out);
   const double ffma16 = rate(fp32_chain<16>, sms, 1 << 16, 16, out);
   const double ffma2_4 = rate(fp32x2_chain<4>, sms, 1 << 16, 8, out);
@@ -194,11 +221,12 @@ int main() {
     }
   }
   printf("{\"sms\": %d, \"max_sm_clock_mhz\": %.0f, \"dfma_per_s\": %.5g, \"dadd_per_s\": %.5g, "
-         "\"dmul_per_s\": %.5g, \"dfma2_dadd1_mix_per_s\": %.5g, \"ffma_scalar_8chains_per_s\": %.5g, "
+         "\"dmul_per_s\": %.5g, \"dfma2_dadd1_mix_per_s\": %.5g, \"dfma_3reg_per_s\": %.5g, "
+         "\"ffma_scalar_8chains_per_s\": %.5g, "
          "\"ffma_scalar_16chains_per_s\": %.5g, \"ffma_packed_8lanes_per_s\": %.5g, "
          "\"ffma_packed_16lanes_per_s\": %.5g, \"packed_vs_scalar_fma_mismatches\": %d, "
          "\"packed_bit_check_values\": %d, \"copy_gbs\": %.1f}\n",
-         sms, clk_khz / 1e3, dfma, dadd, dmul, dmix, ffma8, ffma16, ffma2_4, ffma2_8, mismatches, n, best_gbs);
+         sms, clk_khz / 1e3, dfma, dadd, dmul, dmix, d3reg, ffma8, ffma16, ffma2_4, ffma2_8, mismatches, n, best_gbs);
   free(h);
   return mismatches == 0 ? 0 : 2;
 }
