@@ -27,6 +27,9 @@
  *     allocates device memory; it owns only host-side plan state inside the handle.
  *   - Work is enqueued on the CUDA stream given at creation (NULL = the legacy default
  *     stream) and is asynchronous unless the call says it synchronises.
+ *   - Threads: a handle holds host-side plan state (tables, a cached CUDA graph) and must not
+ *     be used by two host threads at once; distinct handles are independent.  A workspace
+ *     must not be shared by integrations that can overlap on the GPU.
  *   - State layout: [N][D] site-major ("AoS", Fig. 1), contiguous, FP64 (double) for
  *     RK4_FP64 or FP32 (float) for RK4_FP32_KAHAN.  For a batch the chains lie back to
  *     back in the order given at creation.
