@@ -21,6 +21,9 @@ def main():
     ap.add_argument("--tiling", default="256,4,1")
     ap.add_argument("--kernel", choices=["blocked", "staged", "persistent"], default="blocked")
     ap.add_argument("--batch", type=int, default=0, help="integrate this many uneven chains instead of one")
+    ap.add_argument("--tableau", choices=["rk4", "dopri5"], default="rk4",
+                    help="dopri5: the generic kernels with Dormand and Prince's 7-stage tableau")
+    ap.add_argument("--kappa2", type=float, default=0.0, help="second-neighbour coupling (generic kernels)")
     args = ap.parse_args()
 
     import torch
@@ -41,6 +44,11 @@ def main():
     kern = {"blocked": rk.RK4_KERNEL_BLOCKED, "staged": rk.RK4_KERNEL_STAGED,
             "persistent": rk.RK4_KERNEL_PERSISTENT}[args.kernel]
     rk.rk4_chain_set_kernel(h, kern)
+    if args.tableau == "dopri5":
+        import bench
+        rk.rk4_chain_set_tableau(h, bench.DOPRI5_A, bench.DOPRI5_B)
+    if args.kappa2:
+        rk.rk4_chain_set_coupling2(h, args.kappa2)
     rk.rk4_chain_set_tiling(h, *[int(x) for x in args.tiling.split(",")])
     rk.rk4_chain_set_option(h, rk.RK4_OPT_GRAPHS, 0)
     dtype = torch.float64 if prec == rk.RK4_FP64 else torch.float32
