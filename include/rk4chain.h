@@ -328,7 +328,10 @@ int rk4_domain_gather(rk4_domain *d, const void *state, const void *comp, void *
 int rk4_domain_exchange(rk4_domain *d, void *state, void *comp);
 
 /* Advances the domain nsteps >= 0 steps: exchange the ghosts, integrate every part
- * floor(ghost / (s r)) steps (fewer at the end), repeat.  t as for rk4_chain_integrate.
+ * floor(ghost / (s r)) steps (fewer at the end), repeat.  The whole periods of a call run as
+ * one CUDA graph, captured on first use and replayed while the buffers, the step count and the
+ * parts' configuration stay the same.  If t is not NULL it receives n dt, n the steps taken
+ * through this domain so far.
  * Errors: RK4_EINVAL, RK4_ENOMEM_WS, RK4_ECUDA, RK4_EUNSUPPORTED (heterogeneous parameters
  * set on the batch handle, or a scheme whose reach per step exceeds the ghost width). */
 int rk4_domain_integrate(rk4_domain *d, void *state, void *comp, void *ws, size_t ws_bytes,

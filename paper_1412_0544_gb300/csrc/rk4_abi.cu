@@ -90,6 +90,7 @@ struct rk4_chain {
   unsigned gen_version = 0;  // bumped when the tableau or kappa2 changes (graph cache key)
   int auto_kernel = RK4_KERNEL_PERSISTENT;  // scheme RK4_KERNEL_AUTO uses for a batch
   bool timeout_set = false;                 // RK4_OPT_TIMEOUT_NS given explicitly
+  unsigned config_version = 0;              // bumped by every setter (graphs captured by callers)
 };
 
 namespace {
@@ -551,6 +552,28 @@ int rk4d::handle_info(const rk4_chain *h, int *model, bool *fp32, int *nchains, 
   return RK4_OK;
 }
 
+unsigned rk4d::config_version(const rk4_chain *h) { return h->config_version; }
+
+cudaStream_t rk4d::swap_stream(rk4_chain *h, cudaStream_t st) {
+  cudaStream_t old = h->stream;
+  h->stream = st;
+  return old;
+}
+
+bool rk4d::swap_graphs(rk4_chain *h, bool on) {
+  const bool old = h->graphs;
+  h->graphs = on;
+  return old;
+}
+
+int rk4d::prepare_integrate(rk4_chain *h, int64_t nsteps) {
+  if (!h || nsteps < 1) return RK4_EINVAL;
+  if (ensure_pinned(h) != cudaSuccess) return RK4_ECUDA;
+  const int kernel = effective_kernel(h);
+  const Plan P = make_plan(nsteps, kernel == RK4_KERNEL_STAGED ? 1 : h->tiling.k);
+  return prepare_tables(h, P.kval, h->tiling.block * h->tiling.v) == cudaSuccess ? RK4_OK : RK4_ECUDA;
+}
+
 int rk4d::scheme_reach(const rk4_chain *h, int *s, int *range) {
   if (!h) return RK4_EINVAL;
   *s = stages(h);
@@ -638,12 +661,14 @@ int rk4_chain_shape(const rk4_chain *h, int64_t *total_sites, int *dim) {
 
 int rk4_chain_set_kernel(rk4_chain *h, int kernel) {
   if (!h || kernel < RK4_KERNEL_AUTO || kernel > RK4_KERNEL_PERSISTENT) return RK4_EINVAL;
+  h->config_version++;
   h->kernel = kernel;
   return RK4_OK;
 }
 
 int rk4_chain_set_tiling(rk4_chain *h, int block, int v, int k) {
   if (!h) return RK4_EINVAL;
+  h->config_version++;
   if (block == 0) {
     h->tiling_auto = true;
     default_tiling(h);
@@ -758,6 +783,7 @@ int rk4_chain_status(rk4_chain *h, void *ws) {
 
 int rk4_chain_set_option(rk4_chain *h, int option, int64_t value) {
   if (!h) return RK4_EINVAL;
+  h->config_version++;
   if (option == RK4_OPT_GRAPHS) {
     if (value != 0 && value != 1) return RK4_EINVAL;
     h->graphs = value != 0;
@@ -889,6 +915,7 @@ int rk4_chain_autotune(rk4_chain *h, void *state, void *comp, void *ws, size_t w
     return rc != RK4_OK ? rc : RK4_ECUDA;
   }
   if (choose_kernel) h->auto_kernel = best_kernel;
+  h->config_version++;
   h->tiling = best_t;
   h->tiling_auto = false;
   if (best) *best = best_t;
@@ -897,6 +924,7 @@ int rk4_chain_autotune(rk4_chain *h, void *state, void *comp, void *ws, size_t w
 
 int rk4_chain_set_tableau(rk4_chain *h, int s, const double *A, const double *b) {
   if (!h) return RK4_EINVAL;
+  h->config_version++;
   if (s == 0) {  // back to the classical RK4 kernels
     h->has_tableau = false;
     h->tab = classical_rk4();
@@ -925,6 +953,7 @@ int rk4_chain_set_tableau(rk4_chain *h, int s, const double *A, const double *b)
 
 int rk4_chain_set_coupling2(rk4_chain *h, double kappa2) {
   if (!h || !std::isfinite(kappa2)) return RK4_EINVAL;
+  h->config_version++;
   h->kappa2 = kappa2;
   if (!h->has_tableau) h->tab = classical_rk4();
   h->gen_version++;
@@ -935,6 +964,7 @@ int rk4_chain_set_coupling2(rk4_chain *h, double kappa2) {
 int rk4_chain_set_site_params(rk4_chain *h, const void *params) {
   if (!h) return RK4_EINVAL;
   if (params && (reinterpret_cast<uintptr_t>(params) % 16) != 0) return RK4_EINVAL;
+  h->config_version++;
   h->site_params = params;
   default_tiling(h);
   return RK4_OK;

@@ -40,6 +40,13 @@ struct rk4_domain {
   GhostPair *h_pairs = nullptr;   // pinned copy of `pairs`, uploaded to the workspace
   double *h_out = nullptr;        // pinned: per-part energies
   int *h_status = nullptr;        // pinned: status word read-back
+  int64_t nstep = 0;              // steps taken (t = nstep dt)
+  // one CUDA graph of whole exchange periods (exchange + the parts' launches), replayed
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void *g_state = nullptr, *g_comp = nullptr, *g_ws = nullptr;
+  int64_t g_period = 0, g_nper = 0;
+  unsigned g_version = 0;
 };
 
 namespace {
@@ -268,6 +275,70 @@ int rk4_domain_exchange(rk4_domain *d, void *state, void *comp) {
   return exchange(d, state, comp) == cudaSuccess ? RK4_OK : RK4_ECUDA;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Whole exchange periods as one CUDA graph: captured on first use, replayed while the
+// buffers, the period count and the parts' configuration stay the same.
+int run_periods_graph(rk4_domain *d, void *state, void *comp, char *w, const DomLayout &L, int64_t period,
+                      int64_t nper) {
+  // the parts' pinned tables must describe this period's launch plan when the graph runs
+  // (another plan, e.g. a remainder of fewer steps, may have rewritten them since)
+  int rc = prepare_integrate(d->h, period);
+  if (rc != RK4_OK) return rc;
+  const unsigned ver = config_version(d->h);
+  const bool hit = d->gexec && d->g_state == state && d->g_comp == comp && d->g_ws == w && d->g_period == period &&
+                   d->g_nper == nper && d->g_version == ver;
+  if (!hit) {
+    if (d->gexec) {
+      cudaGraphExecDestroy(d->gexec);
+      d->gexec = nullptr;
+    }
+    if (!d->cap && cudaStreamCreateWithFlags(&d->cap, cudaStreamNonBlocking) != cudaSuccess) return RK4_ECUDA;
+    if (cudaStreamBeginCapture(d->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) return RK4_ECUDA;
+    const cudaStream_t old_stream = swap_stream(d->h, d->cap);
+    const bool old_graphs = swap_graphs(d->h, false);
+    double t0 = 0.0;
+    int64_t n0 = 0;
+    rk4_chain_get_clock(d->h, &t0, &n0);
+    const GhostPair *pairs = reinterpret_cast<const GhostPair *>(w + L.pairs);
+    for (int64_t p = 0; p < nper && rc == RK4_OK; ++p) {
+      if (launch_ghost_copy(state, comp, pairs, (int)d->pairs.size(), d->ghost, d->D * (int)d->es, d->cap) !=
+          cudaSuccess)
+        rc = RK4_ECUDA;
+      else
+        rc = rk4_chain_integrate(d->h, state, comp, w, L.batch, period, nullptr);
+    }
+    swap_graphs(d->h, old_graphs);
+    swap_stream(d->h, old_stream);
+    rk4_chain_set_clock(d->h, t0, n0);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(d->cap, &g);
+    if (rc != RK4_OK || e != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      return rc != RK4_OK ? rc : RK4_ECUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&d->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      d->gexec = nullptr;
+      return RK4_ECUDA;
+    }
+    d->g_state = state;
+    d->g_comp = comp;
+    d->g_ws = w;
+    d->g_period = period;
+    d->g_nper = nper;
+    d->g_version = ver;
+  }
+  return cudaGraphLaunch(d->gexec, d->stream) == cudaSuccess ? RK4_OK : RK4_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
 int rk4_domain_integrate(rk4_domain *d, void *state, void *comp, void *ws, size_t ws_bytes, int64_t nsteps,
                          double *t) {
   if (!d || nsteps < 0) return RK4_EINVAL;
@@ -287,19 +358,22 @@ int rk4_domain_integrate(rk4_domain *d, void *state, void *comp, void *ws, size_
   if (period < 1) return RK4_EUNSUPPORTED;
   char *w = static_cast<char *>(ws);
   if (nsteps > 0 && upload_pairs(d, w, L) != cudaSuccess) return RK4_ECUDA;
-  for (int64_t done = 0; done < nsteps;) {
+  int64_t done = 0;
+  const int64_t nper = any_ghost(d) ? nsteps / period : 0;
+  if (nper >= 2) {  // whole periods replayed from one graph
+    const int rc = run_periods_graph(d, state, comp, w, L, period, nper);
+    if (rc != RK4_OK) return rc;
+    done = nper * period;
+  }
+  for (; done < nsteps;) {
     const int64_t m = std::min(period, nsteps - done);
     if (exchange_kernel(d, state, comp, w, L) != cudaSuccess) return RK4_ECUDA;
     const int rc = rk4_chain_integrate(d->h, state, comp, ws, L.batch, m, nullptr);
     if (rc != RK4_OK) return rc;
     done += m;
   }
-  if (t) {
-    double t0 = 0.0;
-    int64_t k = 0;
-    rk4_chain_get_clock(d->h, &t0, &k);
-    *t = t0 + (double)k * d->dt;
-  }
+  d->nstep += nsteps;
+  if (t) *t = (double)d->nstep * d->dt;
   return RK4_OK;
 }
 
@@ -354,6 +428,8 @@ int rk4_domain_status(rk4_domain *d, void *ws) {
 
 int rk4_domain_destroy(rk4_domain *d) {
   if (!d) return RK4_OK;
+  if (d->gexec) cudaGraphExecDestroy(d->gexec);
+  if (d->cap) cudaStreamDestroy(d->cap);
   rk4_chain_destroy(d->h);
   if (d->h_pairs) cudaFreeHost(d->h_pairs);
   if (d->h_out) cudaFreeHost(d->h_out);

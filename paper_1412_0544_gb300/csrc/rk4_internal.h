@@ -158,5 +158,14 @@ int handle_info(const rk4_chain *h, int *model, bool *fp32, int *nchains, const 
 // Stages of the handle's tableau and its coupling range (1, or 2 with second neighbours): one
 // step reaches stages x range sites along the chain.
 int scheme_reach(const rk4_chain *h, int *stages, int *range);
+// For callers that capture a handle's integrations into a larger CUDA graph: a counter bumped
+// by every setter (a captured graph is stale once it changes); the stream the handle enqueues
+// on and its own graph replay, swapped during a capture; and the pinned host tables and
+// buffers an integration of nsteps needs, prepared beforehand (preparing them may synchronise
+// the stream, which must not happen while capturing).
+unsigned config_version(const rk4_chain *h);
+cudaStream_t swap_stream(rk4_chain *h, cudaStream_t st);
+bool swap_graphs(rk4_chain *h, bool on);
+int prepare_integrate(rk4_chain *h, int64_t nsteps);
 
 }  // namespace rk4d

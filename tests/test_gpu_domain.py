@@ -217,3 +217,39 @@ def test_domain_guard_bands(rk):
         assert all(b.intact() for b in bufs)
     finally:
         rk.rk4_domain_destroy(d)
+
+
+def test_domain_graph_replay_and_recapture(rk):
+    """Repeated calls replay the captured graph of whole periods; a remainder of fewer steps in
+    each call runs another launch plan (its batch tables differ), and a tiling change forces a
+    new capture: state and compensation stay bit-identical to the undivided chain."""
+    import torch
+    n, ghost = 30011, 12  # RK4 reaches 4 sites per step: period 3
+    y0 = ci.uniform_state(n, 3, seed=760).astype(np.float32)
+    d = rk.rk4_domain_create(ROE, 1, n, 0.01, PER, 5, ghost, part_lengths=[6000, 12, 9000, 7999, 7000])
+    try:
+        h = rk.rk4_domain_chain(d)
+        rk.rk4_chain_set_tiling(h, 256, 4, 2)
+        rows, D = rk.rk4_domain_shape(d)
+        cst, ccp = tensors(y0, 1)
+        st = torch.zeros((rows, D), dtype=torch.float32, device="cuda")
+        cp = torch.zeros_like(st)
+        ws = torch.empty(rk.rk4_domain_workspace_bytes(d), dtype=torch.uint8, device="cuda")
+        rk.rk4_domain_scatter(d, cst, ccp, st, cp)
+        for _ in range(3):  # 6 whole periods (one graph, replayed) + a 2-step remainder each
+            t = rk.rk4_domain_integrate(d, st, cp, ws, 20)
+        assert t == pytest.approx(60 * 0.01, rel=1e-15)
+        rk.rk4_domain_gather(d, st, cp, cst, ccp)
+        torch.cuda.synchronize()
+        ref, rc, _ = whole(rk, y0, ROE, 1, PER, 60)
+        assert np.array_equal(cst.cpu().numpy(), ref) and np.array_equal(ccp.cpu().numpy(), rc)
+        rk.rk4_chain_set_tiling(h, 128, 8, 3)  # new configuration: captured again
+        for _ in range(2):
+            t = rk.rk4_domain_integrate(d, st, cp, ws, 20)
+        assert t == pytest.approx(100 * 0.01, rel=1e-15)
+        rk.rk4_domain_gather(d, st, cp, cst, ccp)
+        torch.cuda.synchronize()
+        ref, rc, _ = whole(rk, y0, ROE, 1, PER, 100)
+        assert np.array_equal(cst.cpu().numpy(), ref) and np.array_equal(ccp.cpu().numpy(), rc)
+    finally:
+        rk.rk4_domain_destroy(d)
