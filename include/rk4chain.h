@@ -183,7 +183,11 @@ int rk4_chain_step(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_by
 /* Advances the device state nsteps >= 0 RK4 steps in place (stream-ordered).  If t is not
  * NULL it receives t0 + n dt, n being the steps taken through this handle so far (no
  * repeated addition).  Launch sequences of the same shape are replayed from a cached CUDA
- * graph.  Errors: RK4_EINVAL, RK4_ENOMEM_WS, RK4_ECUDA. */
+ * graph.  The blocked scheme makes launches of k steps (the tiling's k) into a ping-pong copy
+ * in ws and must end in `state` after an even number of launches: an odd count is evened by
+ * splitting one launch in two (nsteps = k runs as two launches of k / 2), so calls of an
+ * even multiple of k steps run at the tiling's full k.  Errors: RK4_EINVAL, RK4_ENOMEM_WS,
+ * RK4_ECUDA. */
 int rk4_chain_integrate(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_bytes,
                         int64_t nsteps, double *t);
 
@@ -328,9 +332,9 @@ int rk4_domain_gather(rk4_domain *d, const void *state, const void *comp, void *
 int rk4_domain_exchange(rk4_domain *d, void *state, void *comp);
 
 /* Advances the domain nsteps >= 0 steps: exchange the ghosts, integrate every part
- * floor(ghost / (s r)) steps (fewer at the end), repeat.  The whole periods of a call run as
- * one CUDA graph, captured on first use and replayed while the buffers, the step count and the
- * parts' configuration stay the same.  If t is not NULL it receives n dt, n the steps taken
+ * floor(ghost / (s r)) steps (fewer at the end), repeat.  Whole periods run in chunks of 8 from
+ * one CUDA graph, captured on first use and replayed while the buffers and the parts'
+ * configuration stay the same (calls of any length share it).  If t is not NULL it receives n dt, n the steps taken
  * through this domain so far.
  * Errors: RK4_EINVAL, RK4_ENOMEM_WS, RK4_ECUDA, RK4_EUNSUPPORTED (heterogeneous parameters
  * set on the batch handle, or a scheme whose reach per step exceeds the ghost width). */

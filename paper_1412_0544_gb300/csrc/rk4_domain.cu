@@ -209,8 +209,15 @@ int rk4_domain_create(rk4_domain **out, int model, int precision, int64_t n, dou
     delete d;
     return rc;
   }
-  // few long parts: one blocked launch over all of them is the natural scheme
+  // few long parts: one blocked launch over all of them is the natural scheme.  FP32 runs
+  // several steps per launch (bandwidth-bound at k = 1): an exchange period of P steps runs as
+  // two launches of P / 2 steps (an integration ends in the caller's buffer after an even
+  // number of launches), so that is the default k
   rk4_chain_set_kernel(d->h, RK4_KERNEL_BLOCKED);
+  if (d->fp32 && ghosts) {
+    const int k = (int)std::min<int64_t>(16, std::max<int64_t>(1, ghost / 8));
+    rk4_chain_set_tiling(d->h, 256, 4, k);  // keeps the default if this shape is not valid
+  }
   *out = d;
   return RK4_OK;
 }
@@ -279,10 +286,13 @@ int rk4_domain_exchange(rk4_domain *d, void *state, void *comp) {
 
 namespace {
 
-// Whole exchange periods as one CUDA graph: captured on first use, replayed while the
-// buffers, the period count and the parts' configuration stay the same.
+constexpr int64_t kGraphPeriods = 8;  // exchange periods per captured graph
+
+// A chunk of nper whole exchange periods as one CUDA graph, replayed `reps` times: captured on
+// first use and reused while the buffers, the chunk and the parts' configuration stay the same
+// (the chunk does not depend on a call's step count, so calls of any length share the graph).
 int run_periods_graph(rk4_domain *d, void *state, void *comp, char *w, const DomLayout &L, int64_t period,
-                      int64_t nper) {
+                      int64_t nper, int64_t reps) {
   // the parts' pinned tables must describe this period's launch plan when the graph runs
   // (another plan, e.g. a remainder of fewer steps, may have rewritten them since)
   int rc = prepare_integrate(d->h, period);
@@ -332,7 +342,9 @@ int run_periods_graph(rk4_domain *d, void *state, void *comp, char *w, const Dom
     d->g_nper = nper;
     d->g_version = ver;
   }
-  return cudaGraphLaunch(d->gexec, d->stream) == cudaSuccess ? RK4_OK : RK4_ECUDA;
+  for (int64_t r = 0; r < reps; ++r)
+    if (cudaGraphLaunch(d->gexec, d->stream) != cudaSuccess) return RK4_ECUDA;
+  return RK4_OK;
 }
 
 }  // namespace
@@ -359,11 +371,11 @@ int rk4_domain_integrate(rk4_domain *d, void *state, void *comp, void *ws, size_
   char *w = static_cast<char *>(ws);
   if (nsteps > 0 && upload_pairs(d, w, L) != cudaSuccess) return RK4_ECUDA;
   int64_t done = 0;
-  const int64_t nper = any_ghost(d) ? nsteps / period : 0;
-  if (nper >= 2) {  // whole periods replayed from one graph
-    const int rc = run_periods_graph(d, state, comp, w, L, period, nper);
+  const int64_t reps = any_ghost(d) ? nsteps / (period * kGraphPeriods) : 0;
+  if (reps >= 1) {  // chunks of whole periods replayed from one graph
+    const int rc = run_periods_graph(d, state, comp, w, L, period, kGraphPeriods, reps);
     if (rc != RK4_OK) return rc;
-    done = nper * period;
+    done = reps * kGraphPeriods * period;
   }
   for (; done < nsteps;) {
     const int64_t m = std::min(period, nsteps - done);

@@ -21,6 +21,7 @@ def main():
     ap.add_argument("--tiling", default="256,4,1")
     ap.add_argument("--kernel", choices=["blocked", "staged", "persistent"], default="blocked")
     ap.add_argument("--batch", type=int, default=0, help="integrate this many uneven chains instead of one")
+    ap.add_argument("--parts", type=int, default=0, help="integrate this many equal periodic chains of n / parts")
     ap.add_argument("--tableau", choices=["rk4", "dopri5"], default="rk4",
                     help="dopri5: the generic kernels with Dormand and Prince's 7-stage tableau")
     ap.add_argument("--kappa2", type=float, default=0.0, help="second-neighbour coupling (generic kernels)")
@@ -37,6 +38,11 @@ def main():
     if args.batch:
         lengths, kappa, bcs = ci.batch_spec(args.batch)
         h = rk.rk4_batch_create(model, prec, lengths, kappa, bcs, 0.01)
+        total = int(lengths.sum())
+    elif args.parts:
+        import numpy as np
+        lengths = np.full(args.parts, args.n // args.parts, dtype=np.int64)
+        h = rk.rk4_batch_create(model, prec, lengths, np.ones(args.parts), np.zeros(args.parts, dtype=np.int8), 0.01)
         total = int(lengths.sum())
     else:
         h = rk.rk4_chain_create(model, prec, args.n, 0.01, rk.RK4_PERIODIC)

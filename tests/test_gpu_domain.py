@@ -220,11 +220,12 @@ def test_domain_guard_bands(rk):
 
 
 def test_domain_graph_replay_and_recapture(rk):
-    """Repeated calls replay the captured graph of whole periods; a remainder of fewer steps in
-    each call runs another launch plan (its batch tables differ), and a tiling change forces a
-    new capture: state and compensation stay bit-identical to the undivided chain."""
+    """Repeated calls replay the captured graph of 8 whole periods; between replays the
+    leftover periods and a remainder of fewer steps run other launch plans (a batch's tables
+    differ per plan), and a tiling change forces a new capture: state and compensation stay
+    bit-identical to the undivided chain."""
     import torch
-    n, ghost = 30011, 12  # RK4 reaches 4 sites per step: period 3
+    n, ghost = 30011, 8  # RK4 reaches 4 sites per step: period 2
     y0 = ci.uniform_state(n, 3, seed=760).astype(np.float32)
     d = rk.rk4_domain_create(ROE, 1, n, 0.01, PER, 5, ghost, part_lengths=[6000, 12, 9000, 7999, 7000])
     try:
@@ -236,20 +237,20 @@ def test_domain_graph_replay_and_recapture(rk):
         cp = torch.zeros_like(st)
         ws = torch.empty(rk.rk4_domain_workspace_bytes(d), dtype=torch.uint8, device="cuda")
         rk.rk4_domain_scatter(d, cst, ccp, st, cp)
-        for _ in range(3):  # 6 whole periods (one graph, replayed) + a 2-step remainder each
-            t = rk.rk4_domain_integrate(d, st, cp, ws, 20)
-        assert t == pytest.approx(60 * 0.01, rel=1e-15)
+        for _ in range(3):  # 21 steps: one 8-period graph chunk, 2 more periods, 1 remainder step
+            t = rk.rk4_domain_integrate(d, st, cp, ws, 21)
+        assert t == pytest.approx(63 * 0.01, rel=1e-15)
         rk.rk4_domain_gather(d, st, cp, cst, ccp)
         torch.cuda.synchronize()
-        ref, rc, _ = whole(rk, y0, ROE, 1, PER, 60)
+        ref, rc, _ = whole(rk, y0, ROE, 1, PER, 63)
         assert np.array_equal(cst.cpu().numpy(), ref) and np.array_equal(ccp.cpu().numpy(), rc)
         rk.rk4_chain_set_tiling(h, 128, 8, 3)  # new configuration: captured again
         for _ in range(2):
-            t = rk.rk4_domain_integrate(d, st, cp, ws, 20)
-        assert t == pytest.approx(100 * 0.01, rel=1e-15)
+            t = rk.rk4_domain_integrate(d, st, cp, ws, 21)
+        assert t == pytest.approx(105 * 0.01, rel=1e-15)
         rk.rk4_domain_gather(d, st, cp, cst, ccp)
         torch.cuda.synchronize()
-        ref, rc, _ = whole(rk, y0, ROE, 1, PER, 100)
+        ref, rc, _ = whole(rk, y0, ROE, 1, PER, 105)
         assert np.array_equal(cst.cpu().numpy(), ref) and np.array_equal(ccp.cpu().numpy(), rc)
     finally:
         rk.rk4_domain_destroy(d)
