@@ -8,7 +8,8 @@
 namespace rk4d {
 
 template <typename R, int MODEL, int V, bool KAHAN, bool HET>
-__global__ void __launch_bounds__(max_threads_for(V)) k_blocked(BlockedJob job, Coef<R> cf) {
+__global__ void __launch_bounds__(max_threads_for(V), (V >= 4 && KAHAN && !HET) ? 2 : 0)  // FP32: 2 blocks/SM
+    k_blocked(BlockedJob job, Coef<R> cf) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t item = blockIdx.x;
   ChainDesc ch;
@@ -32,7 +33,7 @@ size_t blocked_smem_bytes(int model, bool fp32, int v, int block, bool het) {
   const int D = model == ROESSLER ? 3 : 2;
   const int P = model == ROESSLER ? 4 : 2;
   const size_t rs = fp32 ? 4 : 8;
-  return 128 * rs + (size_t)block * v * rs * (D * (fp32 ? 2 : 1) + (het ? P : 0));
+  return (size_t)edge_values(v) * rs + (size_t)block * v * rs * (D * (fp32 ? 2 : 1) + (het ? P : 0));
 }
 
 template <typename R, int MODEL, int V, bool KAHAN, bool HET>

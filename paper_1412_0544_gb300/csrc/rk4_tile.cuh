@@ -3,8 +3,8 @@
 // A thread block owns a tile of W = blockDim.x * V consecutive sites of one chain: the G
 // interior sites it will write back plus a halo of H = 4k sites on each side.  Thread t holds
 // sites t*V .. t*V+V-1 in registers.  Every RK stage needs the coupling coordinate of both
-// neighbours: inside a thread it is a register, across lanes a warp shuffle, across warps a
-// two-slot exchange in shared memory (one __syncthreads per stage).  Sites at the tile's
+// neighbours: inside a thread it is a register, across threads an exchange through shared
+// memory (one __syncthreads per stage; see tile_advance).  Sites at the tile's
 // ends read a stand-in value, so after m stages only sites [m, W - m) are exact -- the
 // paper's observation that the error from the missing coupling moves one site inward per
 // stage -- and after 4k stages exactly the interior [4k, W - 4k) is.
@@ -60,6 +60,15 @@ __device__ __forceinline__ void report_nonfinite(WsHeader *hdr, int any) {
 // (about 9 values per site plus temporaries) must fit 65536 registers per block.
 __host__ __device__ constexpr int max_threads_for(int v) { return v <= 1 ? 1024 : (v <= 4 ? 512 : 256); }
 
+// Neighbour exchange of the tile kernels, by sites per thread: with 4 or more, every thread
+// publishes its end values in shared memory (fewer MIO instructions, measured +4-8 % in FP32
+// and +2 % in heterogeneous FP64); with fewer, warp shuffles plus warp-edge slots (the
+// per-thread slots' four address registers cost 6-12 more registers there, which drops a
+// resident block: -12 to -18 %).
+__host__ __device__ constexpr bool thread_exchange(int v) { return v >= 4; }
+// Shared-memory values the exchange takes at the front of a tile kernel's dynamic shared memory.
+__host__ __device__ constexpr int edge_values(int v) { return thread_exchange(v) ? 4 * max_threads_for(v) : 128; }
+
 // Store v to shared memory only when p holds, as a predicated instruction (no divergent
 // branch around it).
 __device__ __forceinline__ void st_shared_if(bool p, float *a, float v) {
@@ -75,21 +84,59 @@ __device__ __forceinline__ void st_shared_if(bool p, double *a, double v) {
                : "memory");
 }
 
-// Advance the registers of one tile by K steps.  `edge` is 4 * 32 values of shared memory:
-// two alternating slots (by stage parity) of [first x of each warp | last x of each warp].
-// Stage 0 of every step reads y directly (it is the stage state), so no register copies are
-// needed between steps.  The warp-edge exchange is branch-free: predicated stores by lanes 0
-// and 31, uniform (broadcast) loads by every lane, and selects.
+// Shared-memory accesses through 32-bit shared-window addresses (four such registers per
+// thread carry the neighbour exchange below; generic pointers would take twice as many).
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void st_shared(unsigned a, float v) {
+  asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_shared(unsigned a, double v) {
+  asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+__device__ __forceinline__ void ld_shared(unsigned a, float &v) {
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+}
+__device__ __forceinline__ void ld_shared(unsigned a, double &v) {
+  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+}
+
+// Advance the registers of one tile by K steps.  `edge` is edge_values(V) values of shared
+// memory, two alternating slots by stage parity.  Per-thread exchange (thread_exchange(V)): a
+// slot is [first x of each thread | last x of each thread], strided by the compile-time
+// largest block so that the per-stage offsets are immediates; every thread stores its two
+// coupling coordinates and, after the stage's one barrier, loads its neighbours'
+// (conflict-free: consecutive threads, consecutive addresses), four shared-memory
+// instructions per warp and stage.  Warp exchange: a slot is [first x of each warp | last x
+// of each warp]; shuffles carry the values inside a warp and lanes 0 and 31 publish theirs by
+// predicated stores, read back as uniform (broadcast) loads and selects.  Either way the two
+// tile ends read a stand-in (their own value), which only ever reaches halo sites.  Stage 0
+// of every step reads y directly (it is the stage state), so no register copies are needed
+// between steps.
 template <typename R, int MODEL, int V, bool KAHAN, bool MASK, bool HET = false>
 __device__ __forceinline__ void tile_advance(R (&y)[V][Dim<MODEL>::D], R (&cmp)[V][Dim<MODEL>::D],
                                              uint32_t ghost, int K, const Coef<R> &cf, R *edge,
                                              const Coef<R> *cs = nullptr) {
   constexpr int D = Dim<MODEL>::D;
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
+  constexpr bool kThread = thread_exchange(V);
+  constexpr int NT = max_threads_for(V);
+  const int tid = threadIdx.x;
+  // per-thread exchange: this thread's slots (parity 0) and its neighbours' (unused and
+  // never computed by the warp exchange)
+  unsigned my_first = 0, my_last = 0, left_last = 0, right_first = 0;
+  if constexpr (kThread) {
+    my_first = smem_addr(edge + tid);
+    my_last = smem_addr(edge + NT + tid);
+    left_last = my_last - (tid > 0 ? (unsigned)sizeof(R) : 0u);
+    right_first = my_first + (tid < (int)blockDim.x - 1 ? (unsigned)sizeof(R) : 0u);
+  }
+  // warp exchange
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
   const int nw = blockDim.x >> 5;
   const bool is_first = lane == 0, is_last = lane == 31;
-  const int prev = (warp > 0) ? warp - 1 : warp;      // tile ends read a stand-in (own warp)
+  const int prev = (warp > 0) ? warp - 1 : warp;
   const int next = (warp < nw - 1) ? warp + 1 : warp;
   R u[V][D], acc[V][D];
   // FP32-Kahan tiles with an even number of sites per thread run on packed instructions
@@ -105,16 +152,26 @@ __device__ __forceinline__ void tile_advance(R (&y)[V][Dim<MODEL>::D], R (&cmp)[
         const R x = (j == 0) ? y[v][0] : u[v][0];
         xs[v] = (MASK && ((ghost >> v) & 1u)) ? R(0) : x;
       }
-      R left = __shfl_up_sync(kFull, xs[V - 1], 1);
-      R right = __shfl_down_sync(kFull, xs[0], 1);
-      R *eb = edge + (j & 1) * 64;  // [0,32): first x of each warp, [32,64): last x
-      st_shared_if(is_first, eb + warp, xs[0]);
-      st_shared_if(is_last, eb + 32 + warp, xs[V - 1]);
-      __syncthreads();
-      const R from_prev = eb[32 + prev];
-      const R from_next = eb[next];
-      left = is_first ? from_prev : left;
-      right = is_last ? from_next : right;
+      R left, right;
+      if constexpr (kThread) {
+        const unsigned po = (j & 1) * 2 * NT * (unsigned)sizeof(R);  // the stage's parity slot
+        st_shared(my_first + po, xs[0]);
+        st_shared(my_last + po, xs[V - 1]);
+        __syncthreads();
+        ld_shared(left_last + po, left);
+        ld_shared(right_first + po, right);
+      } else {
+        left = __shfl_up_sync(kFull, xs[V - 1], 1);
+        right = __shfl_down_sync(kFull, xs[0], 1);
+        R *eb = edge + (j & 1) * 64;  // [0,32): first x of each warp, [32,64): last x
+        st_shared_if(is_first, eb + warp, xs[0]);
+        st_shared_if(is_last, eb + 32 + warp, xs[V - 1]);
+        __syncthreads();
+        const R from_prev = eb[32 + prev];
+        const R from_next = eb[next];
+        left = is_first ? from_prev : left;
+        right = is_last ? from_next : right;
+      }
       if constexpr (kPacked) {
         // sites v and v + 1 in the two halves of packed FP32 instructions
 #pragma unroll
@@ -239,7 +296,8 @@ __device__ __forceinline__ void tile_store(R *__restrict__ dst, const R *tile, i
 }
 
 // Process one (chain, tile) item end to end: load, advance K steps, store the interior.
-// Shared memory: edge[128] | tile[W*D] | ctile[W*D] (Kahan) | ptile[W*P] (heterogeneous).
+// Shared memory: edge[edge_values(V)] | tile[W*D] | ctile[W*D] (Kahan) | ptile[W*P]
+// (heterogeneous).
 // `sites` is the number of sites in the state buffers (for the debug bounds checks); hdr the
 // status word, where a non-finite stored value is reported.
 template <typename R, int MODEL, int V, bool KAHAN, bool COH, bool HET = false>
@@ -250,7 +308,7 @@ __device__ __forceinline__ void tile_item(const R *__restrict__ in, R *__restric
   constexpr int D = Dim<MODEL>::D;
   constexpr int P = Dim<MODEL>::P;
   R *edge = reinterpret_cast<R *>(smem);
-  R *tl = edge + 128;
+  R *tl = edge + edge_values(V);
   const int W = blockDim.x * V;
   R *ctl = tl + W * D;
   R *ptl = ctl + (KAHAN ? W * D : 0);
