@@ -74,8 +74,8 @@ FP32K_INST_PER_SITE_STEP = 61    # + 4 per component for the Kahan update
 # DRAM traffic (read + write bytes) per launch of the FP64 blocked kernel at N = 2^24 from one
 # ncu --set full capture, valid only for the kernel sources (hash) and the tiling recorded with
 # it; any other combination reports null.
-TRAFFIC = {("b134305f0c50d378", "256,4,1"): 402880256 + 356902144,
-           ("b134305f0c50d378", "256,4,2"): 404093184 + 357194752}
+TRAFFIC = {("4b899ca2b1c01b12", "256,4,1"): 402863872 + 357605632,
+           ("4b899ca2b1c01b12", "256,4,2"): 402819840 + 357134336}
 
 
 def kernel_hash() -> str:
