@@ -53,14 +53,16 @@ HBM_GBS_FALLBACK = 6800.0
 FP64_INST_PEAK = 0.6272e12
 FP32_INST_PEAK = 40.12e12
 PEAK_SOURCE = "fallback constants from an earlier pipe_probe run"
+PROBE = {}  # the pipe probe's full result in this run (empty without it)
 
 
 def probe_peaks():
     """Measure the DFMA and FP32 FMA rates with the pipe probe; keep the constants on failure."""
-    global FP64_INST_PEAK, FP32_INST_PEAK, PEAK_SOURCE
+    global FP64_INST_PEAK, FP32_INST_PEAK, PEAK_SOURCE, PROBE
     try:
         from paper_1412_0544_gb300 import pipe_probe
         r = pipe_probe.run()
+        PROBE = r
         FP64_INST_PEAK = float(r["dfma_per_s"])
         FP32_INST_PEAK = float(max(r["ffma_scalar_16chains_per_s"], r["ffma_packed_16lanes_per_s"]))
         PEAK_SOURCE = "of measured: pipe_probe in this run"
@@ -246,6 +248,9 @@ def fp32_kahan_extra(rk, torch, stream, n=1 << 27, nsteps=NSTEPS):
                     "hbm_traffic_GBs_est": sps * 4 * D * 4 * (1 + 8 * best["k"] / best["G"]) / best["k"] / 1e9,
                     "fp32_pipe_frac_of_measured": sps * FP32K_INST_PER_SITE_STEP / FP32_INST_PEAK,
                     "ms_per_launch": 1e3 * el / launches, "half_norm2_t0": e32_0, "half_norm2_fp32": e32})
+        if "rk4_fp32k_regs_lane_ops_per_s" in PROBE:
+            # against the same packed instruction stream on register-resident sites
+            out["frac_of_arithmetic_only"] = sps * FP32K_INST_PER_SITE_STEP / PROBE["rk4_fp32k_regs_lane_ops_per_s"]
         del st, cp, ws
     finally:
         rk.rk4_chain_destroy(h)
@@ -713,6 +718,12 @@ def main():
                 "peak_source": PEAK_SOURCE + " (DFMA issue rate; all 49 operations of the step can issue "
                                              "as DFMA)",
                 "hbm_frac_effective_state": sps_k * 2 * D * 8 / 1e9 / hbm_peak}
+    if probe and "rk4_fp64_regs_inst_per_s" in probe:
+        # the same RK4 instruction stream on register-resident sites (no loads, exchange or
+        # barriers): the most this instruction mix reaches on the FP64 pipe
+        arith_rate = float(probe["rk4_fp64_regs_inst_per_s"])
+        roofline["arithmetic_only_rate"] = arith_rate / 1e9
+        roofline["frac_of_arithmetic_only"] = achieved_inst * 1e9 / arith_rate
 
     # --- end to end through the C ABI with host buffers ------------------------------
     host = torch.empty((n, D), dtype=torch.float64).pin_memory()

@@ -1,8 +1,9 @@
 // pipe_probe.cu -- measures the arithmetic issue rates the integrator's rooflines are quoted
 // against (FP64 DFMA / DADD / DMUL and a 2:1 mix, FP32 FMA issued as scalar and as packed
-// f32x2 instructions) and the device copy bandwidth, and checks that a packed FMA rounds each
-// half exactly like a scalar FMA.  Stand-alone program (not part of librk4chain.so); built and
-// run by pipe_probe.py, it prints one JSON object.
+// f32x2 instructions), the device copy bandwidth and the rate of the integrator's own RK4
+// arithmetic on register-resident sites (FP64, packed FP32-Kahan), and checks that a packed
+// FMA rounds each half exactly like a scalar FMA.  Stand-alone program (not part of
+// librk4chain.so); built and run by pipe_probe.py, it prints one JSON object.
 //
 // Method: every thread runs CH independent dependency chains for `iters` iterations (enough
 // chains to cover the pipe latency), on a grid of `bps` blocks of 256 threads per SM; best of
@@ -11,6 +12,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <cuda_runtime.h>
+
+#include "csrc/rk4_device.cuh"
 
 #define CK(x)                                                                      \
   do {                                                                             \
@@ -125,6 +128,87 @@ __global__ void packed_bit_check(const float *a, const float *b, const float *c,
   if (__float_as_uint(r.x) != __float_as_uint(s0) || __float_as_uint(r.y) != __float_as_uint(s1)) atomicAdd(bad, 1);
 }
 
+// The integrator's own arithmetic stream without memory traffic: the RK4 step of the Roessler
+// chain (the slope and stage functions every tile kernel calls) on 4 register-resident sites
+// per thread, each site's neighbours taken from the thread's own registers -- no loads,
+// no neighbour exchange, no barrier.  Its rate is the most the tile kernels' instruction mix
+// can reach; the tile kernels' distance from it is the cost of everything else.  The
+// coefficients derive from the run-time arguments, so nothing folds at compile time.
+template <int V>
+__global__ void rk4_regs_fp64(double *out, int iters, double a, double b) {
+  constexpr int D = 3;
+  const rk4d::Coef<double> cf{0.2 * a, 1.0 * a, 9.0 * a, a, 1.0, 0.005 * a, 0.01 * a, 0.01 * a / 6.0};
+  double y[V][D], u[V][D], acc[V][D], cmp[V][D];
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      y[v][d] = 0.1 * (d + 1) + 1e-3 * (threadIdx.x + v) + b;
+      cmp[v][d] = 0.0;
+    }
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      double xs[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) xs[v] = (j == 0) ? y[v][0] : u[v][0];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        double k[D];
+        rk4d::slope<double, rk4d::ROESSLER>((j == 0) ? y[v] : u[v], xs[(v + V - 1) % V], xs[(v + 1) % V], cf, k);
+        rk4d::stage_update<double, D, false>(j, k, y[v], u[v], acc[v], cmp[v], cf);
+      }
+    }
+  }
+  double s = 0;
+#pragma unroll
+  for (int v = 0; v < V; ++v) s += y[v][0] + y[v][1] + y[v][2];
+  if (s == -12345.0) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// The same for the FP32-Kahan step on packed f32x2 instructions (two sites per instruction).
+template <int V>
+__global__ void rk4_regs_fp32k(double *out, int iters, double a, double b) {
+  constexpr int D = 3;
+  const float fa = (float)a;
+  const rk4d::Coef<float> c1{0.2f * fa, 1.0f * fa, 9.0f * fa, fa, 1.0f, 0.005f * fa, 0.01f * fa, 0.01f * fa / 6.0f};
+  const rk4d::Coef2 cf = rk4d::pair_coef(c1, c1);
+  float2 y[V / 2][D], u[V / 2][D], acc[V / 2][D], cmp[V / 2][D];
+#pragma unroll
+  for (int p = 0; p < V / 2; ++p)
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      y[p][d] = make_float2(0.1f * (d + 1) + 1e-3f * (threadIdx.x + 2 * p) + (float)b,
+                            0.1f * (d + 1) + 1e-3f * (threadIdx.x + 2 * p + 1) + (float)b);
+      cmp[p][d] = make_float2(0.f, 0.f);
+    }
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float xs[V];
+#pragma unroll
+      for (int p = 0; p < V / 2; ++p) {
+        const float2 x = (j == 0) ? y[p][0] : u[p][0];
+        xs[2 * p] = x.x;
+        xs[2 * p + 1] = x.y;
+      }
+#pragma unroll
+      for (int p = 0; p < V / 2; ++p) {
+        const int v = 2 * p;
+        const float2 xl = make_float2(xs[(v + V - 1) % V], xs[v]);
+        const float2 xr = make_float2(xs[v + 1], xs[(v + 2) % V]);
+        float2 k[D];
+        rk4d::slope2<rk4d::ROESSLER>((j == 0) ? y[p] : u[p], xl, xr, cf, k);
+        rk4d::stage_update2<D>(j, k, y[p], u[p], acc[p], cmp[p], cf);
+      }
+    }
+  }
+  float s = 0;
+#pragma unroll
+  for (int p = 0; p < V / 2; ++p) s += y[p][0].x + y[p][1].y + y[p][2].x + cmp[p][0].y;
+  if (s == -12345.0f) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 __global__ void copy16(const int4 *__restrict__ a, int4 *__restrict__ b, size_t n) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) b[i] = a[i];
@@ -172,6 +256,9 @@ int main() {
   const double ffma16 = rate(fp32_chain<16>, sms, 1 << 16, 16, out);
   const double ffma2_4 = rate(fp32x2_chain<4>, sms, 1 << 16, 8, out);
   const double ffma2_8 = rate(fp32x2_chain<8>, sms, 1 << 16, 16, out);
+  // per thread and iteration: 4 sites x 49 FP64 instructions; 4 sites x 61 FP32 lane-ops
+  const double rk4_fp64 = rate(rk4_regs_fp64<4>, sms, 512, 4 * 49, out);
+  const double rk4_fp32k = rate(rk4_regs_fp32k<4>, sms, 4096, 4 * 61, out);
 
   // bit check on 2^20 operands per input, spread over many binades and both signs
   const int n = 1 << 20;
@@ -225,8 +312,10 @@ int main() {
          "\"ffma_scalar_8chains_per_s\": %.5g, "
          "\"ffma_scalar_16chains_per_s\": %.5g, \"ffma_packed_8lanes_per_s\": %.5g, "
          "\"ffma_packed_16lanes_per_s\": %.5g, \"packed_vs_scalar_fma_mismatches\": %d, "
-         "\"packed_bit_check_values\": %d, \"copy_gbs\": %.1f}\n",
-         sms, clk_khz / 1e3, dfma, dadd, dmul, dmix, d3reg, ffma8, ffma16, ffma2_4, ffma2_8, mismatches, n, best_gbs);
+         "\"packed_bit_check_values\": %d, \"copy_gbs\": %.1f, \"rk4_fp64_regs_inst_per_s\": %.5g, "
+         "\"rk4_fp32k_regs_lane_ops_per_s\": %.5g}\n",
+         sms, clk_khz / 1e3, dfma, dadd, dmul, dmix, d3reg, ffma8, ffma16, ffma2_4, ffma2_8, mismatches, n, best_gbs,
+         rk4_fp64, rk4_fp32k);
   free(h);
   return mismatches == 0 ? 0 : 2;
 }

@@ -18,7 +18,8 @@ EXE = os.path.join(HERE, "_build", "pipe_probe")
 
 def compile_probe() -> str:
     os.makedirs(os.path.dirname(EXE), exist_ok=True)
-    if not os.path.exists(EXE) or os.path.getmtime(EXE) < os.path.getmtime(SRC):
+    deps = (SRC, os.path.join(HERE, "csrc", "rk4_device.cuh"))
+    if not os.path.exists(EXE) or os.path.getmtime(EXE) < max(os.path.getmtime(f) for f in deps):
         cmd = [_build.nvcc(), *_build.ARCH, "-O3", "-std=c++17", "-o", EXE, SRC]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
