@@ -44,12 +44,11 @@ HBM_GBS_FALLBACK = 6800.0
 # Arithmetic peaks for the ALU rooflines, measured by paper_1412_0544_gb300/pipe_probe.cu (run
 # by bench.py itself on rank 0 before the workload, so the denominator comes from the same GPU
 # and clocks; the constants below, from an earlier probe run on a GB300 at 2070 MHz, are the
-# fallback when the probe cannot run).  The classical RK4 Roessler step issues 34 DFMA and
-# 15 DADD per site-step (4 x (4 FMA + 3 ADD) slope, 9 FMA stage states, 6 FMA + 3 ADD sum,
-# 3 FMA update).  Every addition can be issued as an exact FMA (a*1+b), so 49 instructions at
-# the DFMA rate bound the step; a variant built that way gave the same bits and the same
-# time, so the slower DADD rate is not the floor and the roof is the DFMA rate.  FP32: the
-# larger of the scalar and packed (f32x2) FMA lane rates.
+# fallback when the probe cannot run).  The classical RK4 Roessler step issues 41 DFMA and
+# 8 DADD per site-step in FP64 (4 x (5 FMA + 2 ADD) slope, 9 FMA stage states, 12 FMA
+# update).  Every addition can be issued as an exact FMA (a*1+b), so 49 instructions at the
+# DFMA rate bound the step, and the roof is the DFMA rate.  FP32: the larger of the scalar and
+# packed (f32x2) FMA lane rates.
 FP64_INST_PEAK = 0.6272e12
 FP32_INST_PEAK = 40.12e12
 PEAK_SOURCE = "fallback constants from an earlier pipe_probe run"
@@ -71,7 +70,7 @@ def probe_peaks():
         return {"error": str(e)[:200]}
 
 
-FP64_INST_PER_SITE_STEP = 49     # 34 DFMA + 15 DADD
+FP64_INST_PER_SITE_STEP = 49     # 41 DFMA + 8 DADD
 FP32K_INST_PER_SITE_STEP = 61    # + 4 per component for the Kahan update
 # DRAM traffic (read + write bytes) per launch of the FP64 blocked kernel at N = 2^24 from one
 # ncu --set full capture, valid only for the kernel sources (hash) and the tiling recorded with

@@ -169,6 +169,7 @@ CoefD coef(const rk4_chain *h) {
   c.h2 = h->dt / 2.0;
   c.h1 = h->dt;
   c.dt6 = h->dt / 6.0;
+  c.dt3 = h->dt / 3.0;
   c.kappa2 = h->kappa2;
   return c;
 }

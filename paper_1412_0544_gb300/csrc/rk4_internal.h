@@ -19,7 +19,7 @@ struct ChainDesc {
 // Coefficients in double; converted to the working precision once per launch on the host.
 // kappa2: second-neighbour coupling (generic scheme only; 0 for the paper's chain).
 struct CoefD {
-  double a, b, c, kappa, w2, h2, h1, dt6, kappa2;
+  double a, b, c, kappa, w2, h2, h1, dt6, kappa2, dt3;
 };
 
 // Generic explicit Runge-Kutta tableau (strictly lower a, weights b), up to kMaxStages stages.
