@@ -75,8 +75,8 @@ FP32K_INST_PER_SITE_STEP = 61    # + 4 per component for the Kahan update
 # DRAM traffic (read + write bytes) per launch of the FP64 blocked kernel at N = 2^24 from one
 # ncu --set full capture, valid only for the kernel sources (hash) and the tiling recorded with
 # it; any other combination reports null.
-TRAFFIC = {("4b899ca2b1c01b12", "256,4,1"): 402863872 + 357605632,
-           ("4b899ca2b1c01b12", "256,4,2"): 402819840 + 357134336}
+TRAFFIC = {("d5a41b674ada0c58", "256,4,1"): 402786560 + 357420288,
+           ("d5a41b674ada0c58", "256,4,2"): 402934528 + 357470464}
 
 
 def kernel_hash() -> str:

@@ -104,8 +104,9 @@ def test_het_fp32_kahan(rk):
     y0 = ci.uniform_state(n, 3, seed=430).astype(np.float32)
     sp = P.het_params(n, ROE, 431).astype(np.float32)
     st, cst = run(rk, y0, sp, prec=1, nsteps=500, kernel=rk.RK4_KERNEL_STAGED, with_comp=True)
-    got, cgot = run(rk, y0, sp, prec=1, nsteps=500, tiling=(256, 4, 8), with_comp=True)
-    assert np.array_equal(got, st) and np.array_equal(cgot, cst)
+    for tiling in [(256, 4, 8), (256, 2, 8)]:  # per-thread and warp neighbour exchange
+        got, cgot = run(rk, y0, sp, prec=1, nsteps=500, tiling=tiling, with_comp=True)
+        assert np.array_equal(got, st) and np.array_equal(cgot, cst), tiling
     ref = oracle.rk4_integrate_het(y0.astype(np.float64), sp.astype(np.float64), ROE, PER, 0.01, 500)
     err = cf.rel_inf(st - cst, ref)
     print(f"heterogeneous FP32-Kahan, 500 steps: rel err vs FP64 oracle {err:.2e}")

@@ -207,9 +207,11 @@ def test_fp32_kahan_bitwise_and_error(rk, gh):
     y0 = ci.uniform_state(65536, 3).astype(np.float32)
     st, c_st = gh.gpu_run(y0, precision=rk.RK4_FP32_KAHAN, nsteps=1000, kernel=rk.RK4_KERNEL_STAGED,
                           return_comp=True)
-    for tiling in [(256, 4, 4), (256, 8, 8), (512, 4, 16)]:
+    # 1 and 2 sites per thread exchange neighbours by warp shuffles, 4 and 8 by per-thread
+    # shared-memory slots; 2, 4 and 8 run on packed f32x2 instructions, 1 on scalar ones
+    for tiling in [(256, 4, 4), (256, 8, 8), (512, 4, 16), (256, 1, 4), (128, 2, 8)]:
         got, c_got = gh.gpu_run(y0, precision=rk.RK4_FP32_KAHAN, nsteps=1000, tiling=tiling, return_comp=True)
-        assert np.array_equal(got, st) and np.array_equal(c_got, c_st)
+        assert np.array_equal(got, st) and np.array_equal(c_got, c_st), tiling
     ref = oracle.rk4_integrate(y0.astype(np.float64), ROE, PER, 0.01, 1000)
     err = rel(st - c_st, ref)
     print(f"FP32-Kahan Roessler N=65536, 1000 steps: rel err vs FP64 oracle {err:.3e}")
