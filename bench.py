@@ -165,8 +165,9 @@ def host_info() -> dict:
     return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu_model": model}
 
 
-def cpu_baseline(sample_sites: int = 1 << 22, sample_steps: int = 10) -> dict:
-    """The serial C oracle on the host (1 core) on a bounded sample of the workload."""
+def cpu_baseline(sample_sites: int = N_SITES, sample_steps: int = 20) -> dict:
+    """The serial C oracle on the host (1 core) on a bounded sample of the workload: the full
+    chain, 20 of its 1000 RK4 steps (about 15 s on one Grace core)."""
     import chain_inputs as ci
     import oracle
     y0 = ci.uniform_state(sample_sites, D, seed=SEED)
@@ -187,7 +188,7 @@ def run_reference(args):
     import chain_inputs as ci
     import oracle
     oracle.load()
-    sites, steps = 1 << 22, 2
+    sites, steps = N_SITES, 1  # the full chain, one of its RK4 steps per bench step
     y = ci.uniform_state(sites, D, seed=SEED)
     for _ in range(args.warmup):
         y = oracle.rk4_integrate(y, oracle.ROESSLER, oracle.PERIODIC, DT, steps)
@@ -716,7 +717,9 @@ def main():
                 "launch_ms": launch_s * 1e3,
                 "peak_source": PEAK_SOURCE + " (DFMA issue rate; all 49 operations of the step can issue "
                                              "as DFMA)",
-                "hbm_frac_effective_state": sps_k * 2 * D * 8 / 1e9 / hbm_peak}
+                "hbm_frac_effective_state": sps_k * 2 * D * 8 / 1e9 / hbm_peak,
+                # DRAM bandwidth the kernel draws: ncu's bytes per launch over this run's launch time
+                "dram_GBs": traffic / launch_s / 1e9 if traffic else None}
     if probe and "rk4_fp64_regs_inst_per_s" in probe:
         # the same RK4 instruction stream on register-resident sites (no loads, exchange or
         # barriers): the most this instruction mix reaches on the FP64 pipe
