@@ -71,7 +71,7 @@ def probe_peaks():
 
 
 FP64_INST_PER_SITE_STEP = 49     # 41 DFMA + 8 DADD
-FP32K_INST_PER_SITE_STEP = 61    # + 4 per component for the Kahan update
+FP32K_INST_PER_SITE_STEP = 58    # the update: 4 operations per component instead of 1 FMA
 # DRAM traffic (read + write bytes) per launch of the FP64 blocked kernel at N = 2^24 from one
 # ncu --set full capture, valid only for the kernel sources (hash) and the tiling recorded with
 # it; any other combination reports null.

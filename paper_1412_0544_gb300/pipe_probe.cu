@@ -257,9 +257,9 @@ int main() {
   const double ffma16 = rate(fp32_chain<16>, sms, 1 << 16, 16, out);
   const double ffma2_4 = rate(fp32x2_chain<4>, sms, 1 << 16, 8, out);
   const double ffma2_8 = rate(fp32x2_chain<8>, sms, 1 << 16, 16, out);
-  // per thread and iteration: 4 sites x 49 FP64 instructions; 4 sites x 61 FP32 lane-ops
+  // per thread and iteration: 4 sites x 49 FP64 instructions; 4 sites x 58 FP32 lane-ops
   const double rk4_fp64 = rate(rk4_regs_fp64<4>, sms, 512, 4 * 49, out);
-  const double rk4_fp32k = rate(rk4_regs_fp32k<4>, sms, 4096, 4 * 61, out);
+  const double rk4_fp32k = rate(rk4_regs_fp32k<4>, sms, 4096, 4 * 58, out);
 
   // bit check on 2^20 operands per input, spread over many binades and both signs
   const int n = 1 << 20;
