@@ -20,9 +20,10 @@
 //              FP32-Kahan: acc = k1; acc = fma(2, k2, acc); acc = fma(2, k3, acc);
 //              acc = acc + k4; s = fma(dt/6, acc, -c); t = y + s; c = (t - y) - s; y = t
 // The Roessler step costs 49 floating-point instructions per site (4 x 7 slope + 9 stage +
-// 12 update); FP32-Kahan 58 (4 x 7 slope + 9 stage + 9 sum + 12 update).  In FP64 only 8 of the 49 are additions (DADD),
-// the rest DFMA: on GB300 a DADD takes the FP64 pipe longer than a DFMA, and the FP64 forms
-// above run the step 4.7 % faster than the FP32 forms would (same instruction count).
+// 12 update); FP32-Kahan 58 (4 x 7 slope + 9 stage + 9 sum + 12 update).  In FP64 only 8 of
+// the 49 are additions (DADD), the rest DFMA: on GB300 a DADD takes the FP64 pipe longer than
+// a DFMA, and the FP64 forms above run the step 4.7 % faster than the FP32 forms would (same
+// instruction count).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
