@@ -64,7 +64,7 @@ extern "C" {
 #define RK4_ECUDA (-3)         /* a CUDA runtime call failed */
 #define RK4_ENONFINITE (-4)    /* a NaN or infinity was found in the state */
 #define RK4_ETIMEOUT (-5)      /* a bounded device-side wait gave up */
-#define RK4_EUNSUPPORTED (-6)  /* valid request this build does not support */
+#define RK4_EUNSUPPORTED (-6)  /* valid request the library does not support */
 #define RK4_EBOUNDS (-7)       /* debug build only: an index check caught an out-of-range access
                                   (the access was skipped); see the build notes below */
 
