@@ -50,6 +50,9 @@ def test_argument_validation_without_gpu(rk):
         rk.rk4_batch_create(0, 0, [10, 5], [1.0, float("inf")], [0, 0], 0.01)
     with pytest.raises(E):
         rk.rk4_batch_create(0, 0, [10, 5], [1.0, 1.0], [0, 3], 0.01)
+    with pytest.raises(E) as ei:  # an empty batch
+        rk.rk4_batch_create(0, 0, [], [], [], 0.01)
+    assert ei.value.code == rk.RK4_EINVAL
 
 
 def test_tiling_rules(rk):
