@@ -736,6 +736,11 @@ def main():
         arith_rate = float(probe["rk4_fp64_regs_inst_per_s"])
         roofline["arithmetic_only_rate"] = arith_rate / 1e9
         roofline["frac_of_arithmetic_only"] = achieved_inst * 1e9 / arith_rate
+    if probe and "rk4_fp64_regs_smem_roundtrip_inst_per_s" in probe:
+        # the same stream with a tile kernel's per-stage shared-memory exchange and barrier
+        xrate = float(probe["rk4_fp64_regs_smem_roundtrip_inst_per_s"])
+        roofline["arithmetic_with_exchange_rate"] = xrate / 1e9
+        roofline["frac_of_arithmetic_with_exchange"] = achieved_inst * 1e9 / xrate
 
     # --- end to end through the C ABI with host buffers ------------------------------
     host = torch.empty((n, D), dtype=torch.float64).pin_memory()

@@ -134,9 +134,14 @@ __global__ void packed_bit_check(const float *a, const float *b, const float *c,
 // no neighbour exchange, no barrier.  Its rate is the most the tile kernels' instruction mix
 // can reach; the tile kernels' distance from it is the cost of everything else.  The
 // coefficients derive from the run-time arguments, so nothing folds at compile time.
-template <int V>
+// ROUNDTRIP: every stage each thread also stores its two edge values to shared memory and,
+// after a barrier, reads them back as its neighbours -- the same values and arithmetic, plus
+// the shared-memory traffic and barrier a tile kernel's neighbour exchange has.
+template <int V, bool ROUNDTRIP = false>
 __global__ void rk4_regs_fp64(double *out, int iters, double a, double b) {
   constexpr int D = 3;
+  __shared__ double slot[ROUNDTRIP ? 2 * 2 * 256 : 1];
+  const int tid = threadIdx.x;
   const rk4d::Coef<double> cf{0.2 * a, 1.0 * a, 9.0 * a, a, 1.0, 0.005 * a, 0.01 * a, 0.01 * a / 6.0, 0.01 * a / 3.0};
   double y[V][D], u[V][D], acc[V][D], cmp[V][D];
 #pragma unroll
@@ -152,10 +157,20 @@ __global__ void rk4_regs_fp64(double *out, int iters, double a, double b) {
       double xs[V];
 #pragma unroll
       for (int v = 0; v < V; ++v) xs[v] = (j == 0) ? y[v][0] : u[v][0];
+      double left = xs[V - 1], right = xs[0];
+      if constexpr (ROUNDTRIP) {
+        double *eb = slot + (j & 1) * 2 * 256;
+        eb[tid] = xs[0];
+        eb[256 + tid] = xs[V - 1];
+        __syncthreads();
+        left = eb[256 + tid];
+        right = eb[tid];
+      }
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         double k[D];
-        rk4d::slope<double, rk4d::ROESSLER>((j == 0) ? y[v] : u[v], xs[(v + V - 1) % V], xs[(v + 1) % V], cf, k);
+        rk4d::slope<double, rk4d::ROESSLER>((j == 0) ? y[v] : u[v], v == 0 ? left : xs[v - 1],
+                                            v == V - 1 ? right : xs[v + 1], cf, k);
         rk4d::stage_update<double, D, false>(j, k, y[v], u[v], acc[v], cmp[v], cf);
       }
     }
@@ -259,6 +274,7 @@ int main() {
   const double ffma2_8 = rate(fp32x2_chain<8>, sms, 1 << 16, 16, out);
   // per thread and iteration: 4 sites x 49 FP64 instructions; 4 sites x 58 FP32 lane-ops
   const double rk4_fp64 = rate(rk4_regs_fp64<4>, sms, 512, 4 * 49, out);
+  const double rk4_fp64_rt = rate(rk4_regs_fp64<4, true>, sms, 512, 4 * 49, out);
   const double rk4_fp32k = rate(rk4_regs_fp32k<4>, sms, 4096, 4 * 58, out);
 
   // bit check on 2^20 operands per input, spread over many binades and both signs
@@ -314,9 +330,9 @@ int main() {
          "\"ffma_scalar_16chains_per_s\": %.5g, \"ffma_packed_8lanes_per_s\": %.5g, "
          "\"ffma_packed_16lanes_per_s\": %.5g, \"packed_vs_scalar_fma_mismatches\": %d, "
          "\"packed_bit_check_values\": %d, \"copy_gbs\": %.1f, \"rk4_fp64_regs_inst_per_s\": %.5g, "
-         "\"rk4_fp32k_regs_lane_ops_per_s\": %.5g}\n",
+         "\"rk4_fp32k_regs_lane_ops_per_s\": %.5g, \"rk4_fp64_regs_smem_roundtrip_inst_per_s\": %.5g}\n",
          sms, clk_khz / 1e3, dfma, dadd, dmul, dmix, d3reg, ffma8, ffma16, ffma2_4, ffma2_8, mismatches, n, best_gbs,
-         rk4_fp64, rk4_fp32k);
+         rk4_fp64, rk4_fp32k, rk4_fp64_rt);
   free(h);
   return mismatches == 0 ? 0 : 2;
 }

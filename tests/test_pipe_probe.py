@@ -16,7 +16,7 @@ def test_probe_rates_and_packed_bit_identity():
     r = pipe_probe.run()
     assert r["packed_vs_scalar_fma_mismatches"] == 0 and r["packed_bit_check_values"] > 0
     for key in ("dfma_per_s", "dadd_per_s", "ffma_scalar_16chains_per_s", "ffma_packed_16lanes_per_s", "copy_gbs",
-                "rk4_fp64_regs_inst_per_s", "rk4_fp32k_regs_lane_ops_per_s"):
+                "rk4_fp64_regs_inst_per_s", "rk4_fp32k_regs_lane_ops_per_s", "rk4_fp64_regs_smem_roundtrip_inst_per_s"):
         assert r[key] > 0, key
     # every FP64 instruction of the step can issue as a DFMA: the stream cannot beat that rate
     assert r["rk4_fp64_regs_inst_per_s"] <= 1.02 * r["dfma_per_s"]
