@@ -114,21 +114,29 @@ __global__ void __launch_bounds__(256) k_gen_combine(GenStagedJob job, Tableau<R
 
 // ---- temporally blocked generic kernel ----------------------------------------------------
 
-// Advance one tile's registers K steps of the generic scheme.  `edge`: 2 parities x 4 slots x
-// 32 warps = 256 values of shared memory (slots: first two and last two coupling coordinates
-// of each warp).
+// Two values of the working precision as one 8- or 16-byte shared-memory access.
+template <typename R> struct Pair;
+template <> struct Pair<float> { using T = float2; };
+template <> struct Pair<double> { using T = double2; };
+
+// Advance one tile's registers K steps of the generic scheme.  `edge`: gen_edge_values(V)
+// values of shared memory, two parities of [(first, second) coupling coordinate of each thread
+// | (second-last, last) of each thread].  Every stage each thread stores its two pairs (two
+// vector stores) and, after the stage's one barrier, reads its left neighbour's last pair and
+// its right neighbour's first pair (two vector loads, conflict-free): four shared-memory
+// instructions for the range-2 coupling, where shuffles plus warp-edge slots took 12 (FP32) or
+// 16 (FP64).  The two tile ends read a stand-in (their own pair), which only reaches halo sites.
 template <typename R, int MODEL, int V, int RANGE, bool KAHAN, bool MASK>
 __device__ __forceinline__ void gen_tile_advance(R (&y)[V][Dim<MODEL>::D], R (&cmp)[V][Dim<MODEL>::D],
                                                  uint32_t ghost, int K, const Coef<R> &cf, R kappa2,
                                                  const Tableau<R> &tb, R *edge) {
   constexpr int D = Dim<MODEL>::D;
-  static_assert(RANGE == 1 || V >= 2, "second-neighbour coupling needs two sites per thread");
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
-  const bool is_first = lane == 0, is_last = lane == 31;
-  const int prev = (warp > 0) ? warp - 1 : warp;
-  const int next = (warp < nw - 1) ? warp + 1 : warp;
+  static_assert(V >= 2, "the generic kernel holds at least two sites per thread");
+  constexpr int NT = gen_max_threads(V);
+  using R2 = typename Pair<R>::T;
+  const int tid = threadIdx.x;
+  const int lt = tid > 0 ? tid - 1 : tid;                           // left neighbour thread
+  const int rt = tid < (int)blockDim.x - 1 ? tid + 1 : tid;          // right neighbour thread
   R k[V][kMaxStages][D];
 
   int parity = 0;  // edge slots alternate strictly from stage to stage (s may be odd)
@@ -144,30 +152,24 @@ __device__ __forceinline__ void gen_tile_advance(R (&y)[V][Dim<MODEL>::D], R (&c
         gen_stage_state<R, D>(j, tb, y[v], k[v], u[v]);
         ext[2 + v] = (MASK && ((ghost >> v) & 1u)) ? R(0) : u[v][0];
       }
-      ext[1] = __shfl_up_sync(kFull, ext[V + 1], 1);
-      ext[V + 2] = __shfl_down_sync(kFull, ext[2], 1);
-      if constexpr (RANGE == 2) {
-        ext[0] = __shfl_up_sync(kFull, ext[V], 1);
-        ext[V + 3] = __shfl_down_sync(kFull, ext[3], 1);
-      }
-      R *eb = edge + parity * 128;  // [0,32) first x, [32,64) second x, [64,96) last x, [96,128) second-last
+      R2 *head = reinterpret_cast<R2 *>(edge) + parity * 2 * NT;  // (first, second) per thread
+      R2 *tail = head + NT;                                         // (second-last, last) per thread
       parity ^= 1;
-      st_shared_if(is_first, eb + warp, ext[2]);
-      st_shared_if(is_last, eb + 64 + warp, ext[V + 1]);
-      if constexpr (RANGE == 2) {
-        st_shared_if(is_first, eb + 32 + warp, ext[3]);
-        st_shared_if(is_last, eb + 96 + warp, ext[V]);
-      }
+      R2 hv, tv;
+      hv.x = ext[2];
+      hv.y = ext[3];
+      tv.x = ext[V];
+      tv.y = ext[V + 1];
+      head[tid] = hv;
+      tail[tid] = tv;
       __syncthreads();
       {
-        const R p1 = eb[64 + prev], n1 = eb[next];
-        ext[1] = is_first ? p1 : ext[1];
-        ext[V + 2] = is_last ? n1 : ext[V + 2];
-        if constexpr (RANGE == 2) {
-          const R p2 = eb[96 + prev], n2 = eb[32 + next];
-          ext[0] = is_first ? p2 : ext[0];
-          ext[V + 3] = is_last ? n2 : ext[V + 3];
-        }
+        const R2 l = tail[lt];
+        const R2 r = head[rt];
+        ext[0] = l.x;
+        ext[1] = l.y;
+        ext[V + 2] = r.x;
+        ext[V + 3] = r.y;
       }
 #pragma unroll
       for (int v = 0; v < V; ++v) {
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(gen_max_threads(V)) k_gen_blocked(BlockedJob j
   constexpr int D = Dim<MODEL>::D;
   extern __shared__ __align__(16) unsigned char smem[];
   R *edge = reinterpret_cast<R *>(smem);
-  R *tl = edge + 256;
+  R *tl = edge + gen_edge_values(V);
   const int W = blockDim.x * V;
   R *ctl = tl + W * D;
   const int64_t item = blockIdx.x;
@@ -274,7 +276,7 @@ int gen_blocked_max_threads(int model, bool fp32, int range, int v) {
 size_t gen_blocked_smem_bytes(int model, bool fp32, int v, int block) {
   const int D = model == ROESSLER ? 3 : 2;
   const size_t rs = fp32 ? 4 : 8;
-  return 256 * rs + (size_t)block * v * D * rs * (fp32 ? 2 : 1);
+  return (size_t)gen_edge_values(v) * rs + (size_t)block * v * D * rs * (fp32 ? 2 : 1);
 }
 
 // ---- launchers ------------------------------------------------------------------------------

@@ -9,6 +9,9 @@ namespace rk4d {
 // Largest block of the generic tile kernel by sites per thread (it keeps every stage slope
 // of every site in registers).
 __host__ __device__ constexpr int gen_max_threads(int v) { return v <= 4 ? 256 : 128; }
+// Shared-memory values of the generic tile kernel's neighbour exchange: 2 parities x 2 pairs
+// of coupling coordinates per thread of the largest block.
+__host__ __device__ constexpr int gen_edge_values(int v) { return 2 * 4 * gen_max_threads(v); }
 
 // The tableau in the working precision: a_jm dt and b_m dt rounded once on the host, plus
 // bit masks of the nonzero entries (zero entries are skipped, in every kernel alike).
