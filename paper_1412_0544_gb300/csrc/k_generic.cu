@@ -126,7 +126,7 @@ template <> struct Pair<double> { using T = double2; };
 // its right neighbour's first pair (two vector loads, conflict-free): four shared-memory
 // instructions for the range-2 coupling, where shuffles plus warp-edge slots took 12 (FP32) or
 // 16 (FP64).  The two tile ends read a stand-in (their own pair), which only reaches halo sites.
-template <typename R, int MODEL, int V, int RANGE, bool KAHAN, bool MASK>
+template <typename R, int MODEL, int V, int RANGE, bool KAHAN, bool MASK, uint64_t SHAPE>
 __device__ __forceinline__ void gen_tile_advance(R (&y)[V][Dim<MODEL>::D], R (&cmp)[V][Dim<MODEL>::D],
                                                  uint32_t ghost, int K, const Coef<R> &cf, R kappa2,
                                                  const Tableau<R> &tb, R *edge) {
@@ -144,12 +144,12 @@ __device__ __forceinline__ void gen_tile_advance(R (&y)[V][Dim<MODEL>::D], R (&c
   for (int s = 0; s < K; ++s) {
 #pragma unroll
     for (int j = 0; j < kMaxStages; ++j) {
-      if (j >= tb.s) break;
+      if (j >= gen_stages<SHAPE>(tb)) break;
       R u[V][D];
       R ext[V + 4];  // ext[2 + v] = x of site v; two neighbours on each side
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        gen_stage_state<R, D>(j, tb, y[v], k[v], u[v]);
+        gen_stage_state<R, D, SHAPE>(j, tb, y[v], k[v], u[v]);
         ext[2 + v] = (MASK && ((ghost >> v) & 1u)) ? R(0) : u[v][0];
       }
       R2 *head = reinterpret_cast<R2 *>(edge) + parity * 2 * NT;  // (first, second) per thread
@@ -181,11 +181,11 @@ __device__ __forceinline__ void gen_tile_advance(R (&y)[V][Dim<MODEL>::D], R (&c
       }
     }
 #pragma unroll
-    for (int v = 0; v < V; ++v) gen_combine<R, D, KAHAN>(tb, k[v], y[v], cmp[v]);
+    for (int v = 0; v < V; ++v) gen_combine<R, D, KAHAN, SHAPE>(tb, k[v], y[v], cmp[v]);
   }
 }
 
-template <typename R, int MODEL, int V, int RANGE, bool KAHAN>
+template <typename R, int MODEL, int V, int RANGE, bool KAHAN, uint64_t SHAPE = 0>
 __global__ void __launch_bounds__(gen_max_threads(V)) k_gen_blocked(BlockedJob job, Coef<R> cf, R kappa2,
                                                                      Tableau<R> tb, int H) {
   constexpr int D = Dim<MODEL>::D;
@@ -229,9 +229,9 @@ __global__ void __launch_bounds__(gen_max_threads(V)) k_gen_blocked(BlockedJob j
       const int64_t g = t0 + base + v;
       if (g < 0 || g >= ch.n) ghost |= 1u << v;
     }
-    gen_tile_advance<R, MODEL, V, RANGE, KAHAN, true>(y, cmp, ghost, job.K, c, kappa2, tb, edge);
+    gen_tile_advance<R, MODEL, V, RANGE, KAHAN, true, SHAPE>(y, cmp, ghost, job.K, c, kappa2, tb, edge);
   } else {
-    gen_tile_advance<R, MODEL, V, RANGE, KAHAN, false>(y, cmp, 0u, job.K, c, kappa2, tb, edge);
+    gen_tile_advance<R, MODEL, V, RANGE, KAHAN, false, SHAPE>(y, cmp, 0u, job.K, c, kappa2, tb, edge);
   }
   const int64_t g0 = t0 + H;
   const int64_t rem = ch.n - g0;
@@ -302,6 +302,29 @@ static Tableau<R> to_tableau(const TableauD &t, double dt) {
   return r;
 }
 
+// The nonzero pattern of a tableau (see shape_a_bit): the key of the compiled shapes.
+static uint64_t tableau_shape(const TableauD &t) {
+  uint64_t sh = (uint64_t)t.s & 7u;
+  for (int j = 1; j < t.s; ++j)
+    for (int m = 0; m < j; ++m)
+      if (t.a[j][m] != 0.0) sh |= shape_a_bit(j, m);
+  for (int m = 0; m < t.s; ++m)
+    if (t.b[m] != 0.0) sh |= shape_b_bit(m);
+  return sh;
+}
+
+// Shapes with tile kernels compiled for them (4 sites per thread): the classical RK4 tableau
+// (the generic kernel runs it with second-neighbour coupling) and Dormand-Prince 5 (7 stages,
+// a_61 = 0, b_1 = b_6 = 0).  Other tableaux run the kernel that reads the pattern at run time.
+constexpr uint64_t kShapeRK4 = 4u | shape_a_bit(1, 0) | shape_a_bit(2, 1) | shape_a_bit(3, 2) | shape_b_bit(0) |
+                               shape_b_bit(1) | shape_b_bit(2) | shape_b_bit(3);
+constexpr uint64_t kShapeDopri5 =
+    7u | shape_a_bit(1, 0) | shape_a_bit(2, 0) | shape_a_bit(2, 1) | shape_a_bit(3, 0) | shape_a_bit(3, 1) |
+    shape_a_bit(3, 2) | shape_a_bit(4, 0) | shape_a_bit(4, 1) | shape_a_bit(4, 2) | shape_a_bit(4, 3) |
+    shape_a_bit(5, 0) | shape_a_bit(5, 1) | shape_a_bit(5, 2) | shape_a_bit(5, 3) | shape_a_bit(5, 4) |
+    shape_a_bit(6, 0) | shape_a_bit(6, 2) | shape_a_bit(6, 3) | shape_a_bit(6, 4) | shape_a_bit(6, 5) |
+    shape_b_bit(0) | shape_b_bit(2) | shape_b_bit(3) | shape_b_bit(4) | shape_b_bit(5);
+
 static int64_t staged_grid(int64_t total) {
   int64_t g = (total + 255) / 256;
   return g > 152 * 64 ? 152 * 64 : (g < 1 ? 1 : g);
@@ -338,21 +361,32 @@ cudaError_t launch_gen_staged_step(int model, bool fp32, int range, const GenSta
 #undef RK4_GEN_STAGED
 }
 
-template <typename R, int MODEL, int V, int RANGE, bool KAHAN>
-static cudaError_t gen_blocked_t(int block, const BlockedJob &job, const CoefD &cfd, const TableauD &td, double dt,
+template <typename R, int MODEL, int V, int RANGE, bool KAHAN, uint64_t SHAPE>
+static cudaError_t gen_blocked_s(int block, const BlockedJob &job, const CoefD &cfd, const TableauD &td, double dt,
                                  int H, cudaStream_t st) {
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_gen_blocked<R, MODEL, V, RANGE, KAHAN>,
+    attr_err = cudaFuncSetAttribute(k_gen_blocked<R, MODEL, V, RANGE, KAHAN, SHAPE>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
   if (attr_err != cudaSuccess) return attr_err;
   if (job.ntiles <= 0) return cudaSuccess;
   const size_t smem = gen_blocked_smem_bytes(MODEL, KAHAN, V, block);
-  k_gen_blocked<R, MODEL, V, RANGE, KAHAN><<<(unsigned)job.ntiles, block, smem, st>>>(
+  k_gen_blocked<R, MODEL, V, RANGE, KAHAN, SHAPE><<<(unsigned)job.ntiles, block, smem, st>>>(
       job, to_coef<R>(cfd, cfd.kappa), (R)cfd.kappa2, to_tableau<R>(td, dt), H);
   return cudaGetLastError();
+}
+
+template <typename R, int MODEL, int V, int RANGE, bool KAHAN>
+static cudaError_t gen_blocked_t(int block, const BlockedJob &job, const CoefD &cfd, const TableauD &td, double dt,
+                                 int H, cudaStream_t st) {
+  if constexpr (V == 4) {
+    const uint64_t sh = tableau_shape(td);
+    if (sh == kShapeDopri5) return gen_blocked_s<R, MODEL, V, RANGE, KAHAN, kShapeDopri5>(block, job, cfd, td, dt, H, st);
+    if (sh == kShapeRK4) return gen_blocked_s<R, MODEL, V, RANGE, KAHAN, kShapeRK4>(block, job, cfd, td, dt, H, st);
+  }
+  return gen_blocked_s<R, MODEL, V, RANGE, KAHAN, 0>(block, job, cfd, td, dt, H, st);
 }
 
 template <int MODEL, int RANGE>

@@ -23,14 +23,30 @@ template <typename R> struct Tableau {
   uint32_t bnz;
 };
 
+// The nonzero pattern of a tableau ("shape") packed into one word, for kernels compiled for a
+// fixed tableau: the stage count in bits 0-2, a_jm (m < j) at bit 3 + j (j - 1) / 2 + m, b_m
+// at bit 24 + m.  SHAPE = 0 reads the pattern from the tableau at run time.  Either way the
+// same zero entries are skipped, so both forms perform the same operations.
+__host__ __device__ constexpr uint64_t shape_a_bit(int j, int m) { return 1ull << (3 + j * (j - 1) / 2 + m); }
+__host__ __device__ constexpr uint64_t shape_b_bit(int m) { return 1ull << (24 + m); }
+template <uint64_t SHAPE, typename R> __device__ __forceinline__ int gen_stages(const Tableau<R> &tb) {
+  if constexpr (SHAPE != 0) return (int)(SHAPE & 7u); else return tb.s;
+}
+template <uint64_t SHAPE, typename R> __device__ __forceinline__ bool gen_a_nonzero(const Tableau<R> &tb, int j, int m) {
+  if constexpr (SHAPE != 0) return (SHAPE & shape_a_bit(j, m)) != 0; else return (tb.anz[j] >> m) & 1u;
+}
+template <uint64_t SHAPE, typename R> __device__ __forceinline__ bool gen_b_nonzero(const Tableau<R> &tb, int m) {
+  if constexpr (SHAPE != 0) return (SHAPE & shape_b_bit(m)) != 0; else return (tb.bnz >> m) & 1u;
+}
+
 // Eq. (4): stage state of stage j from the step's start y and the earlier slopes.
-template <typename R, int D>
+template <typename R, int D, uint64_t SHAPE = 0>
 __device__ __forceinline__ void gen_stage_state(int j, const Tableau<R> &tb, const R *y, const R (*k)[D], R *u) {
 #pragma unroll
   for (int d = 0; d < D; ++d) u[d] = y[d];
 #pragma unroll
   for (int m = 0; m < kMaxStages; ++m) {
-    if (m < j && ((tb.anz[j] >> m) & 1u)) {
+    if (m < j && gen_a_nonzero<SHAPE>(tb, j, m)) {
 #pragma unroll
       for (int d = 0; d < D; ++d) u[d] = fma(tb.adt[j][m], k[m][d], u[d]);
     }
@@ -50,7 +66,10 @@ __device__ __forceinline__ void slope_gen(const R *u, R xl, R xr, R xl2, R xr2, 
     if constexpr (MODEL == ROESSLER) {
       k[0] = fma(cf.kappa, lap, fma(kappa2, lap2, -add(u[1], u[2])));
       k[1] = fma(cf.a, u[1], u[0]);
-      k[2] = fma(u[2], sub(u[0], cf.c), cf.b);
+      if constexpr (sizeof(R) == 8)
+        k[2] = fma(u[2], u[0], fma(-cf.c, u[2], cf.b));  // as slope(): two DFMA, no DADD
+      else
+        k[2] = fma(u[2], sub(u[0], cf.c), cf.b);
     } else {
       k[0] = u[1];
       k[1] = fma(cf.kappa, lap, fma(kappa2, lap2, -mul(cf.w2, u[0])));
@@ -59,14 +78,14 @@ __device__ __forceinline__ void slope_gen(const R *u, R xl, R xr, R xl2, R xr2, 
 }
 
 // Eq. (5): y += sum_m b_m dt k_m, in FP64 or with a Kahan-compensated update in FP32.
-template <typename R, int D, bool KAHAN>
+template <typename R, int D, bool KAHAN, uint64_t SHAPE = 0>
 __device__ __forceinline__ void gen_combine(const Tableau<R> &tb, const R (*k)[D], R *y, R *cmp) {
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     R inc = R(0);
 #pragma unroll
     for (int m = 0; m < kMaxStages; ++m)
-      if (m < tb.s && ((tb.bnz >> m) & 1u)) inc = fma(tb.bdt[m], k[m][d], inc);
+      if (m < gen_stages<SHAPE>(tb) && gen_b_nonzero<SHAPE>(tb, m)) inc = fma(tb.bdt[m], k[m][d], inc);
     if constexpr (KAHAN) {
       const R s = sub(inc, cmp[d]);
       const R t = add(y[d], s);
