@@ -465,11 +465,18 @@ DOPRI5_B = np.array([35 / 384, 0, 500 / 1113, 125 / 192, -2187 / 6784, 11 / 84, 
 
 
 def generic_fp_ops(A, b, D, slope_ops, kahan):
-    """Floating-point instructions per site-step of the generic kernel: stage-state FMAs, slopes,
-    weighted sum, update (FP32-Kahan: 4 per component instead of 1)."""
+    """Algorithmic floating-point instructions per site-step of the generic scheme: the slopes
+    and stage states of the stages the result needs (a stage is needed when its weight b_m is
+    nonzero or a needed later stage uses it; Dormand-Prince 5's seventh stage, with b_7 = 0,
+    is not), the weighted sum and the update (FP32-Kahan: 4 per component instead of 1)."""
     s = len(b)
-    return (int(np.count_nonzero(np.tril(A, -1))) * D + s * slope_ops + int(np.count_nonzero(b)) * D
-            + (4 if kahan else 1) * D)
+    A = np.tril(np.asarray(A, dtype=float), -1)
+    needed = {m for m in range(s) if b[m] != 0}
+    for j in range(s - 1, -1, -1):
+        if j in needed:
+            needed |= {m for m in range(j) if A[j][m] != 0}
+    return (sum(int(np.count_nonzero(A[j])) for j in needed) * D + len(needed) * slope_ops
+            + int(np.count_nonzero(b)) * D + (4 if kahan else 1) * D)
 
 
 def variant_extra(rk, torch, stream, precision, *, generic=False, het=False, n=N_SITES, nsteps=200):
