@@ -145,6 +145,7 @@ __device__ __forceinline__ void gen_tile_advance(R (&y)[V][Dim<MODEL>::D], R (&c
 #pragma unroll
     for (int j = 0; j < kMaxStages; ++j) {
       if (j >= gen_stages<SHAPE>(tb)) break;
+      if (!gen_stage_needed<SHAPE>(j)) continue;  // a compiled shape's dead stage: nothing reads it
       R u[V][D];
       R ext[V + 4];  // ext[2 + v] = x of site v; two neighbours on each side
 #pragma unroll

@@ -112,9 +112,27 @@ bool use_generic(const rk4_chain *h) { return h->has_tableau || h->kappa2 != 0.0
 bool use_het(const rk4_chain *h) { return h->site_params != nullptr; }
 int coupling_range(const rk4_chain *h) { return h->kappa2 != 0.0 ? 2 : 1; }
 int stages(const rk4_chain *h) { return use_generic(h) ? h->tab.s : 4; }
+// Stages the step's result depends on: those with a nonzero weight b_m and, recursively, the
+// earlier stages a needed stage uses.  A stage outside this set (Dormand-Prince 5's seventh,
+// with b_7 = 0) cannot influence y, so the dependency cone of one step spans at most this
+// many stages: the tile halo and the sub-domain reach are sized by it.
+int needed_stages(const rk4_chain *h) {
+  if (!use_generic(h)) return 4;
+  const TableauD &t = h->tab;
+  uint32_t need = 0;
+  for (int m = 0; m < t.s; ++m)
+    if (t.b[m] != 0.0) need |= 1u << m;
+  for (int j = t.s - 1; j >= 0; --j)
+    if ((need >> j) & 1u)
+      for (int m = 0; m < j; ++m)
+        if (t.a[j][m] != 0.0) need |= 1u << m;
+  int n = 0;
+  for (int m = 0; m < t.s; ++m) n += (need >> m) & 1u;
+  return n;
+}
 
 // Halo per side of one launch of k steps: s stages, each reaching `range` sites further.
-int halo(const rk4_chain *h, int k) { return stages(h) * coupling_range(h) * k; }
+int halo(const rk4_chain *h, int k) { return needed_stages(h) * coupling_range(h) * k; }
 
 TableauD classical_rk4() {
   TableauD t{};
@@ -577,7 +595,7 @@ int rk4d::prepare_integrate(rk4_chain *h, int64_t nsteps) {
 
 int rk4d::scheme_reach(const rk4_chain *h, int *s, int *range) {
   if (!h) return RK4_EINVAL;
-  *s = stages(h);
+  *s = needed_stages(h);
   *range = coupling_range(h);
   return RK4_OK;
 }

@@ -29,6 +29,22 @@ template <typename R> struct Tableau {
 // same zero entries are skipped, so both forms perform the same operations.
 __host__ __device__ constexpr uint64_t shape_a_bit(int j, int m) { return 1ull << (3 + j * (j - 1) / 2 + m); }
 __host__ __device__ constexpr uint64_t shape_b_bit(int m) { return 1ull << (24 + m); }
+// Stages of a compiled shape that the result needs (bit m set): nonzero weight, or used by a
+// needed later stage.  The others are skipped outright, exchange included.
+__host__ __device__ constexpr uint32_t shape_needed(uint64_t shape) {
+  const int s = (int)(shape & 7u);
+  uint32_t need = 0;
+  for (int m = 0; m < s; ++m)
+    if (shape & shape_b_bit(m)) need |= 1u << m;
+  for (int j = s - 1; j >= 0; --j)
+    if ((need >> j) & 1u)
+      for (int m = 0; m < j; ++m)
+        if (shape & shape_a_bit(j, m)) need |= 1u << m;
+  return need;
+}
+template <uint64_t SHAPE> __device__ __forceinline__ constexpr bool gen_stage_needed(int j) {
+  if constexpr (SHAPE != 0) return (shape_needed(SHAPE) >> j) & 1u; else return true;
+}
 template <uint64_t SHAPE, typename R> __device__ __forceinline__ int gen_stages(const Tableau<R> &tb) {
   if constexpr (SHAPE != 0) return (int)(SHAPE & 7u); else return tb.s;
 }

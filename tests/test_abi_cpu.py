@@ -177,6 +177,14 @@ def test_generic_scheme_validation(rk):
             rk.rk4_chain_set_tiling(h, 256, 1, 1)
         rk.rk4_chain_set_tiling(h, 128, 4, 3)
         assert rk.rk4_chain_get_tiling(h)["G"] == 512 - 2 * 18
+        # Dormand-Prince 5: the seventh stage has weight 0 and feeds nothing, so the halo covers
+        # the six stages the result needs
+        import oracle_pins as P
+        Ad, bd, _ = P.TABLEAUX["dopri5"]
+        rk.rk4_chain_set_tableau(h, Ad, bd)
+        rk.rk4_chain_set_tiling(h, 128, 4, 3)
+        assert rk.rk4_chain_get_tiling(h)["G"] == 512 - 2 * 6 * 2 * 3
+        rk.rk4_chain_set_tableau(h, A, np.array([1 / 6, 2 / 3, 1 / 6]))
         rk.rk4_chain_set_kernel(h, rk.RK4_KERNEL_STAGED)
         assert rk.rk4_chain_workspace_bytes(h) >= 4 * 1000 * 3 * 8  # stage state + 3 slopes
         rk.rk4_chain_set_tableau(h)  # back to classical RK4 (still range 2)

@@ -122,7 +122,8 @@ def test_decomposition_on_oracle_bitwise(rk, model, bc, nparts, ghost, lengths):
 
 
 def test_decomposition_generic_scheme_on_oracle(rk):
-    """Dormand-Prince 5 with second-neighbour coupling reaches 7 x 2 = 14 sites per step."""
+    """Dormand-Prince 5 with second-neighbour coupling reaches at most 7 x 2 = 14 sites per step
+    (12 counting only the stages the result needs); exchanging for 14 is safe either way."""
     A, b, _ = P.TABLEAUX["dopri5"]
     prm = oracle.params(kappa2=0.4)
     y0 = ci.uniform_state(1500, 3, seed=610)

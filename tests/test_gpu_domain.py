@@ -127,8 +127,9 @@ def test_domain_every_scheme(rk, kernel, tiling):
 
 
 def test_domain_generic_scheme(rk):
-    """Dormand-Prince 5 with second neighbours: 14 sites of reach per step, ghost 28 gives two
-    steps per exchange; the ghost bonds of the second-neighbour energy end inside the ghosts."""
+    """Dormand-Prince 5 with second neighbours: 12 sites of reach per step (6 needed stages x
+    2; the seventh stage feeds nothing), ghost 28 gives two steps per exchange; the ghost bonds
+    of the second-neighbour energy end inside the ghosts."""
     A, b, _ = P.TABLEAUX["dopri5"]
 
     def setup(h):
@@ -169,9 +170,9 @@ def test_domain_errors(rk):
         assert ei.value.code == rk.RK4_EINVAL
         h = rk.rk4_domain_chain(d)
         A, b, _ = P.TABLEAUX["dopri5"]
-        rk.rk4_chain_set_tableau(h, A, b)  # reach 7 <= ghost 8: one step per exchange
+        rk.rk4_chain_set_tableau(h, A, b)  # reach 6 <= ghost 8: one step per exchange
         rk.rk4_domain_integrate(d, st, None, ws, 2)
-        rk.rk4_chain_set_coupling2(h, 0.3)  # reach 14 > 8
+        rk.rk4_chain_set_coupling2(h, 0.3)  # reach 12 > 8
         with pytest.raises(rk.RK4Error) as ei:
             rk.rk4_domain_integrate(d, st, None, ws, 1)
         assert ei.value.code == rk.RK4_EUNSUPPORTED
