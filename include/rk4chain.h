@@ -92,8 +92,9 @@ typedef struct {
 } rk4_params;
 
 /* Tiling of the blocked kernels: a tile is block * v sites, of which G = block * v - 2 H are
- * written back, H = 4k (classical RK4) or s * range * k (generic scheme) being the halo on each
- * side. */
+ * written back, H = 4k (classical RK4) or s' * range * k (generic scheme) being the halo on each
+ * side; s' counts the stages the step's result needs (those with a nonzero weight and the
+ * stages they use), e.g. 6 of Dormand-Prince 5's 7. */
 typedef struct {
   int block;  /* threads per block: 64 .. 1024, a multiple of 32 */
   int v;      /* consecutive sites per thread: 1, 2, 4 or 8 (generic kernels: 2 or 4) */
@@ -144,7 +145,8 @@ int rk4_chain_get_tiling(const rk4_chain *h, rk4_tiling *out);
  * stages (the paper notes the technique applies to any explicit RK method, Sec. 2): A is s x s
  * row-major and must be strictly lower triangular, b holds the s weights (Eqs. (4)-(5)); both
  * are copied.  s = 0 restores the classical RK4 kernels.  The generic kernels keep every stage
- * slope per site and need a halo of s * range sites per side per step; tilings then use v = 2
+ * slope per site and need a halo of s' * range sites per side per step (s' <= s: the stages
+ * the result needs; a stage with weight 0 that no such stage uses is not); tilings then use v = 2
  * or 4 sites per thread.  The persistent kernel does not support them (RK4_EUNSUPPORTED).
  * Resets the tiling to its default.  Errors: RK4_EINVAL. */
 int rk4_chain_set_tableau(rk4_chain *h, int s, const double *A, const double *b);
@@ -269,8 +271,8 @@ int rk4_fill_uniform(void *dst, int64_t count, uint64_t seed, uint64_t start, in
  * exchanges: Sec. 2.3's granularity with overlap (a cluster plus s sites of overlap per side
  * per step, recomputed redundantly) applied to memory partitions -- the form a chain takes
  * when it is spread over several memories, with one neighbour exchange every few steps.
- * An s-stage scheme with coupling range r moves information s r sites per step, so the
- * parts run floor(ghost / (s r)) steps between exchanges (ghost / 4 for classical RK4 with
+ * A scheme whose result needs s stages, with coupling range r, moves information s r sites per
+ * step, so the parts run floor(ghost / (s r)) steps between exchanges (ghost / 4 for classical RK4 with
  * nearest neighbours), and every interior site performs the same operations as in the
  * undivided chain: the gathered result is bit-identical to rk4_chain_integrate on the whole
  * chain with the same model, precision, parameters and tableau.
