@@ -481,9 +481,8 @@ def generic_fp_ops(A, b, D, slope_ops, kahan):
 
 def variant_extra(rk, torch, stream, precision, *, generic=False, het=False, n=N_SITES, nsteps=200):
     """The widened scheme on the same N = 2^24 periodic Roessler chain: Dormand-Prince 5 with
-    second-neighbour coupling (generic kernel, halo 12 sites per side per step: six needed stages x
-    range 2), or a
-    heterogeneous chain with per-site parameters (Eq. (1))."""
+    second-neighbour coupling (generic kernel, halo 12 sites per side per step: six needed
+    stages x range 2), or a heterogeneous chain with per-site parameters (Eq. (1))."""
     import chain_inputs as ci
     fp32 = precision == rk.RK4_FP32_KAHAN
     dtype = torch.float32 if fp32 else torch.float64
