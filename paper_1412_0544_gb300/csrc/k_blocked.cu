@@ -7,8 +7,21 @@
 
 namespace rk4d {
 
+// Largest block and resident blocks per SM the blocked kernel is compiled for.  FP32 with 4+
+// sites per thread asks for two blocks of the largest size (64 registers); the heterogeneous
+// FP32 Roessler chain with 4 sites per thread, whose four per-site coefficients need more, is
+// capped at 256 threads and asks for three such blocks (79 registers instead of 96, which
+// allowed two).  Elsewhere no minimum: an explicit minimum of one block lets ptxas take more
+// registers.
+template <int MODEL, int V, bool KAHAN, bool HET> struct BlockedBounds {
+  static constexpr bool kHetWide = HET && KAHAN && V == 4 && MODEL == ROESSLER;
+  static constexpr int threads = kHetWide ? 256 : max_threads_for(V);
+  static constexpr int min_blocks = kHetWide ? 3 : ((V >= 4 && KAHAN && !HET) ? 2 : 0);
+};
+
 template <typename R, int MODEL, int V, bool KAHAN, bool HET>
-__global__ void __launch_bounds__(max_threads_for(V), (V >= 4 && KAHAN && !HET) ? 2 : 0)  // FP32: 2 blocks/SM
+__global__ void __launch_bounds__(BlockedBounds<MODEL, V, KAHAN, HET>::threads,
+                                  BlockedBounds<MODEL, V, KAHAN, HET>::min_blocks)
     k_blocked(BlockedJob job, Coef<R> cf) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t item = blockIdx.x;
