@@ -76,8 +76,8 @@ FP32K_INST_PER_SITE_STEP = 58    # the update: 4 operations per component instea
 # DRAM traffic (read + write bytes) per launch of the FP64 blocked kernel at N = 2^24 from one
 # ncu --set full capture, valid only for the kernel code (kernel_hash) and the tiling recorded
 # with it; any other combination reports null.
-TRAFFIC = {("68d9d39138b4d0f1", "256,4,1"): 402786560 + 357420288,
-           ("68d9d39138b4d0f1", "256,4,2"): 402934528 + 357470464}
+TRAFFIC = {("b5a04136b0356ff4", "256,4,1"): 402816512 + 357019136,
+           ("b5a04136b0356ff4", "256,4,2"): 403300864 + 356990976}
 
 
 def code_only(src: str) -> str:
