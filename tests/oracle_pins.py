@@ -338,6 +338,25 @@ def pin_nnn_cone(lib, n=96, site=48):
     return ok, f"NNN cone {detail}"
 
 
+def pin_dopri5_nnn_cone(lib, n=160, site=80):
+    """Dormand-Prince 5 with second neighbours: the seventh stage has weight 0 and no stage uses
+    it, so one step's influence spreads through the six stages the result needs, exactly 2 x 6
+    = 12 sites per step (not 14) -- the halo and sub-domain reach the GPU path sizes by."""
+    A, b, _ = TABLEAUX["dopri5"]
+    y0 = ci.uniform_state(n, 3, seed=9310)
+    y1 = y0.copy()
+    y1[site, 0] += 0.5
+    prm = oracle.params(kappa=5.0, kappa2=10.0)
+    detail, ok = [], True
+    for m in (1, 2, 3):
+        a = oracle.rk_integrate(y0, A, b, ROE, FIX, 0.05, m, prm, lib=lib)
+        c = oracle.rk_integrate(y1, A, b, ROE, FIX, 0.05, m, prm, lib=lib)
+        changed = np.nonzero(np.any(a != c, axis=1))[0]
+        detail.append((m, int(changed.min()), int(changed.max())))
+        ok &= changed.min() == site - 12 * m and changed.max() == site + 12 * m
+    return ok, f"Dormand-Prince 5 + NNN cone {detail}"
+
+
 # ---- heterogeneous chains, Eq. (1): site-dependent f_i and g_i ---------------------------
 
 def het_params(n, model, seed, kappa_scale=1.0):
@@ -449,6 +468,7 @@ ALL_PINS = [
     ("nnn_modal", pin_nnn_modal),
     ("nnn_energy_fixed", pin_nnn_energy_fixed),
     ("nnn_cone", pin_nnn_cone),
+    ("dopri5_nnn_cone", pin_dopri5_nnn_cone),
     ("nnn_dop853_fix", lambda lib: pin_roessler_vs_dop853(lib, bc=FIX, kappa=1.2, kappa2=0.7)),
     ("nnn_brute_per", lambda lib: pin_brute_force(lib, n=5, model=ROE, bc=PER, kappa2=0.9)),
     ("nnn_brute_fix", lambda lib: pin_brute_force(lib, n=6, model=HAR, bc=FIX, kappa2=0.9)),
