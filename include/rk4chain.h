@@ -137,7 +137,10 @@ int rk4_chain_set_kernel(rk4_chain *h, int kernel);
 int rk4_chain_get_kernel(const rk4_chain *h, int *kernel);
 
 /* Sets the tiling (block, v, k; G is computed).  block = 0 restores the automatic choice.
- * Errors: RK4_EINVAL when block, v or k is out of range or G < 8k. */
+ * The largest block depends on the kernel the handle runs (its register budget): 1024
+ * threads for v = 1, 512 for v = 2 and 4, 256 for v = 8, the generic scheme and the
+ * heterogeneous FP32 Roessler chain with v = 4.  Errors: RK4_EINVAL when block, v or k is out
+ * of range for the kernel or G < 8k (G < 2 * halo for the generic scheme). */
 int rk4_chain_set_tiling(rk4_chain *h, int block, int v, int k);
 int rk4_chain_get_tiling(const rk4_chain *h, rk4_tiling *out);
 
