@@ -140,7 +140,7 @@ int rk4_chain_get_kernel(const rk4_chain *h, int *kernel);
  * The largest block depends on the kernel the handle runs (its register budget): 1024
  * threads for v = 1, 512 for v = 2 and 4, 256 for v = 8, the generic scheme and the
  * heterogeneous FP32 Roessler chain with v = 4.  Errors: RK4_EINVAL when block, v or k is out
- * of range for the kernel or G < 8k (G < 2 * halo for the generic scheme). */
+ * of range for the kernel or G < 8k (for the generic scheme: G < its halo per side). */
 int rk4_chain_set_tiling(rk4_chain *h, int block, int v, int k);
 int rk4_chain_get_tiling(const rk4_chain *h, rk4_tiling *out);
 
