@@ -8,7 +8,9 @@ the GPU name, model, precision, number of chains, total sites rounded to a power
 caller-supplied scheme tag (for example the tableau and coupling range); the value is the
 kernel and the (block, v, k) tiling.  Writes replace the file atomically; two processes
 writing at once can lose one entry, never corrupt the file.  A cached choice is a tiling the
-autotuner once measured fastest: results are bit-identical whichever tiling runs.
+autotuner once measured fastest: results are bit-identical whichever tiling runs.  An entry
+the library rejects when it is applied (written by a build with other kernel limits) is tuned
+again and replaced.
 """
 from __future__ import annotations
 
@@ -61,7 +63,8 @@ def autotune(h, state, comp, ws, key: str, *, probe_steps: int = 16, path: str |
     default to rk4_chain_autotune, rk4_chain_set_kernel + rk4_chain_set_tiling and
     rk4_chain_get_kernel (they can be replaced, e.g. to test the cache without a GPU).
     Without a path (argument or RK4CHAIN_TUNE_CACHE) this is plain rk4_chain_autotune."""
-    from . import (rk4_chain_autotune, rk4_chain_get_kernel, rk4_chain_set_kernel, rk4_chain_set_tiling)
+    from . import (RK4Error, rk4_chain_autotune, rk4_chain_get_kernel, rk4_chain_set_kernel,
+                   rk4_chain_set_tiling)
     tuner = tuner or (lambda: rk4_chain_autotune(h, state, comp, ws, probe_steps))
     get_kernel = get_kernel or (lambda: rk4_chain_get_kernel(h))
 
@@ -74,8 +77,11 @@ def autotune(h, state, comp, ws, key: str, *, probe_steps: int = 16, path: str |
     if path:
         entry = load(path).get(key)
         if entry and all(f in entry for f in ("kernel", "block", "v", "k")):
-            apply(entry)
-            return dict(entry, cached=True)
+            try:
+                apply(entry)
+                return dict(entry, cached=True)
+            except RK4Error:
+                pass  # a stale entry (a tiling the library no longer accepts): tune again
     best = dict(tuner())
     best["kernel"] = int(get_kernel())
     if path:

@@ -66,3 +66,18 @@ def test_incomplete_entries_are_not_applied(tmp_path):
     r = tc.autotune(None, None, None, None, "k", path=path, tuner=lambda: {"block": 64, "v": 2, "k": 1},
                     apply=lambda e: pytest.fail("incomplete entry applied"), get_kernel=lambda: 2)
     assert r["cached"] is False
+
+
+def test_stale_entries_are_tuned_again(tmp_path):
+    """An entry the library rejects when applied (a tiling another build allowed) is replaced."""
+    from paper_1412_0544_gb300 import RK4Error
+    path = str(tmp_path / "t.json")
+    tc.store(path, "k", {"kernel": 2, "block": 512, "v": 4, "k": 16})
+
+    def reject(entry):
+        raise RK4Error(-1, "rk4_chain_set_tiling")
+
+    r = tc.autotune(None, None, None, None, "k", path=path, tuner=lambda: {"block": 256, "v": 4, "k": 16, "G": 896},
+                    apply=reject, get_kernel=lambda: 2)
+    assert r["cached"] is False and r["block"] == 256
+    assert tc.load(path)["k"] == {"kernel": 2, "block": 256, "v": 4, "k": 16, "G": 896}
