@@ -224,3 +224,26 @@ def test_checkpoint_file_round_trip(rk, tmp_path):
     with pytest.raises(rk.RK4Error):
         rk.rk4_chain_set_clock(h, 0.0, -1)
     rk.rk4_chain_destroy(h)
+
+
+def test_generic_halo_counts_needed_stages(rk):
+    """The generic halo is (stages the result needs) x range x k: a stage with weight 0 that no
+    needed stage uses cannot influence the step (host logic, no GPU)."""
+    h = rk.rk4_chain_create(0, 0, 4000, 0.01, 0)
+    try:
+        def G_for(A, b, k=2):
+            rk.rk4_chain_set_tableau(h, np.array(A, dtype=float), np.array(b, dtype=float))
+            rk.rk4_chain_set_tiling(h, 128, 4, k)
+            return rk.rk4_chain_get_tiling(h)["G"]
+        # all three stages needed
+        assert G_for([[0, 0, 0], [0.5, 0, 0], [-1, 2, 0]], [1 / 6, 2 / 3, 1 / 6]) == 512 - 2 * 3 * 2
+        # only the first stage has weight and nothing uses the others: one stage
+        assert G_for([[0, 0, 0], [0.5, 0, 0], [0, 1.0, 0]], [1.0, 0, 0]) == 512 - 2 * 1 * 2
+        # the last stage uses the first only: stages 1 and 3 needed, the middle one dead
+        assert G_for([[0, 0, 0], [0.5, 0, 0], [1.0, 0, 0]], [0, 0, 1.0]) == 512 - 2 * 2 * 2
+        # a weightless stage that a needed stage uses is needed
+        assert G_for([[0, 0, 0], [0.5, 0, 0], [0, 1.0, 0]], [0, 0, 1.0]) == 512 - 2 * 3 * 2
+        rk.rk4_chain_set_coupling2(h, 0.3)  # range 2 doubles the halo
+        assert G_for([[0, 0, 0], [0.5, 0, 0], [1.0, 0, 0]], [0, 0, 1.0]) == 512 - 2 * 2 * 2 * 2
+    finally:
+        rk.rk4_chain_destroy(h)
