@@ -1,17 +1,19 @@
 """Benchmark: site-steps/s of classical RK4 on the paper's coupled Roessler chain on GB300.
 
-Workload (one "step" of this benchmark = one pass of the whole hot path): a periodic Roessler
-chain (Eqs. (6)-(7), a = 0.2, b = 1, c = 9, kappa = 1) of N = 2^24 sites in FP64, i.i.d.
-uniform[-1, 1) initial state from the counter-based generator, advanced 1000 RK4 steps with
-dt = 0.01 by the temporally blocked kernel (tiling chosen by the autotuner), followed by one
-FP64 norm reduction with non-finite check.  The state (403 MB) and its ping-pong copy are
-larger than the 129 MB L2, so no flush is needed between steps.
+Workload (one "step" of this benchmark = one pass of the whole hot path): a fixed-end Roessler
+chain (Eqs. (6)-(7), a = 0.2, b = 1, c = 9, kappa = 1) of N = 2^27 sites in FP64 (3.2 GB of
+state), i.i.d. uniform[-1, 1) initial state from the counter-based generator, advanced 200 RK4
+steps with dt = 0.01 by the temporally blocked kernel (tiling chosen by the autotuner),
+followed by one FP64 norm reduction with non-finite check.  This is the largest single-GPU
+chain configuration; the state and its ping-pong copy are far larger than the 129 MB L2, so no
+flush is needed between steps.
 
 Printed: one JSON line (rank 0).  `value` = site-steps/s over all ranks; `roofline` refers to
 the blocked FP64 kernel, which is bound by the FP64 pipe (49 FP64 instructions per site-step
 against the measured FP64 FMA rate of this GPU); `e2e` measures the same through
 rk4_chain_integrate_host from pinned host memory; `cpu_baseline` is the serial C oracle on the
-host.  Extra keys report the FP32-Kahan path and a batch of uneven chains.
+host.  Extra keys report the periodic N = 2^24 chain, the FP32-Kahan path, batches of uneven
+chains and the widened schemes.
 
 `--impl reference` times the CPU oracle instead (the reference arm), on bounded samples.
 """
@@ -35,14 +37,15 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "site-steps/s (RK4, fp64 & fp32-compensated) and % of GB300 HBM roofline"
-WORKLOAD = "roessler_chain_fp64_N2^24_1000steps"
-N_SITES = 1 << 24
+WORKLOAD = "roessler_chain_fp64_fixed_N2^27_200steps"
+N_HEAD, NSTEPS_HEAD, BC_HEAD = 1 << 27, 200, "fixed"  # the timed workload
+N_SITES = 1 << 24  # the periodic chain of the extra measurements and the sweeps
 NSTEPS = 1000
 DT = 0.01
 SEED = 0x14120544
 D = 3
 HBM_GBS_FALLBACK = 6800.0
-# Arithmetic peaks for the ALU rooflines, measured by paper_1412_0544_gb300/pipe_probe.cu (run
+# Arithmetic peaks for the ALU rooflines, measured by pipe_probe.cu beside this file (run
 # by bench.py itself on rank 0 before the workload, so the denominator comes from the same GPU
 # and clocks; the constants below, from an earlier probe run on a GB300 at 2070 MHz, are the
 # fallback when the probe cannot run).  The classical RK4 Roessler step issues 41 DFMA and
@@ -60,7 +63,7 @@ def probe_peaks():
     """Measure the DFMA and FP32 FMA rates with the pipe probe; keep the constants on failure."""
     global FP64_INST_PEAK, FP32_INST_PEAK, PEAK_SOURCE, PROBE
     try:
-        from paper_1412_0544_gb300 import pipe_probe
+        import pipe_probe
         r = pipe_probe.run()
         PROBE = r
         FP64_INST_PEAK = float(r["dfma_per_s"])
@@ -73,11 +76,18 @@ def probe_peaks():
 
 FP64_INST_PER_SITE_STEP = 49     # 41 DFMA + 8 DADD
 FP32K_INST_PER_SITE_STEP = 58    # the update: 4 operations per component instead of 1 FMA
-# DRAM traffic (read + write bytes) per launch of the FP64 blocked kernel at N = 2^24 from one
-# ncu --set full capture, valid only for the kernel code (kernel_hash) and the tiling recorded
-# with it; any other combination reports null.
-TRAFFIC = {("b5a04136b0356ff4", "256,4,1"): 402816512 + 357019136,
-           ("b5a04136b0356ff4", "256,4,2"): 403300864 + 356990976}
+# DRAM traffic (read + write bytes) per launch of the FP64 blocked kernel from one ncu capture,
+# with the chain length it was taken at: valid only for the kernel code (kernel_hash) and the
+# tiling recorded with it; any other combination reports null.  A launch's traffic is
+# proportional to the sites it advances (one read and one write of each tile), so a capture at
+# N = 2^24 scales to the N = 2^27 workload by the site count.
+TRAFFIC = {}
+
+
+def traffic_per_launch(khash: str, tiling: dict, n: int):
+    """ncu DRAM bytes per launch for this kernel code and tiling, scaled to n sites, or None."""
+    rec = TRAFFIC.get((khash, f"{tiling['block']},{tiling['v']},{tiling['k']}"))
+    return None if rec is None else rec[0] * n / rec[1]
 
 
 def code_only(src: str) -> str:
@@ -175,44 +185,48 @@ def host_info() -> dict:
     return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu_model": model}
 
 
-def cpu_baseline(sample_sites: int = N_SITES, sample_steps: int = 20) -> dict:
-    """The serial C oracle on the host (1 core) on a bounded sample of the workload: the full
-    chain, 20 of its 1000 RK4 steps (about 15 s on one Grace core)."""
+def cpu_baseline(sample_sites: int = 1 << 24, sample_steps: int = 20) -> dict:
+    """The serial C oracle on the host (1 core) on a bounded sample of the workload: a
+    fixed-end chain made of the workload's first 2^24 sites (the same per-site work), 20 RK4
+    steps (about 15 s on one Grace core)."""
     import chain_inputs as ci
     import oracle
     y0 = ci.uniform_state(sample_sites, D, seed=SEED)
     oracle.load()
     t0 = time.perf_counter()
-    oracle.rk4_integrate(y0, oracle.ROESSLER, oracle.PERIODIC, DT, sample_steps)
+    oracle.rk4_integrate(y0, oracle.ROESSLER, oracle.FIXED, DT, sample_steps)
     dt = time.perf_counter() - t0
     return {"value": sample_sites * sample_steps / dt, "unit": "site-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"periodic Roessler chain N={sample_sites}, {sample_steps} RK4 steps, FP64, serial C oracle"}
+            "sample": f"fixed-end Roessler chain of the workload's first {sample_sites} sites, {sample_steps} "
+                      "RK4 steps, FP64, serial C oracle"}
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle, timed on bounded samples of the same workload."""
-    from paper_1412_0544_gb300 import dist
-    rank, world, _ = dist.env_rank()
+    """Reference arm: the CPU oracle, timed on bounded samples of the same workload.  Only the
+    oracle runs here: the rank comes from the launcher's environment, and the CUDA library is
+    never loaded into this process."""
+    rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import chain_inputs as ci
     import oracle
     oracle.load()
-    sites, steps = N_SITES, 1  # the full chain, one of its RK4 steps per bench step
+    sites, steps = 1 << 24, 2  # the workload's first 2^24 sites as a fixed-end chain, 2 RK4 steps per step
     y = ci.uniform_state(sites, D, seed=SEED)
     for _ in range(args.warmup):
-        y = oracle.rk4_integrate(y, oracle.ROESSLER, oracle.PERIODIC, DT, steps)
+        y = oracle.rk4_integrate(y, oracle.ROESSLER, oracle.FIXED, DT, steps)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        y = oracle.rk4_integrate(y, oracle.ROESSLER, oracle.PERIODIC, DT, steps)
+        y = oracle.rk4_integrate(y, oracle.ROESSLER, oracle.FIXED, DT, steps)
     el = time.perf_counter() - t0
     value = sites * steps * args.steps / el
-    sample = f"periodic Roessler chain N={sites}, {steps} RK4 steps per step, FP64, serial C oracle"
+    sample = (f"fixed-end Roessler chain of the workload's first {sites} sites, {steps} RK4 steps per step, "
+              "FP64, serial C oracle")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "site-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sites": N_SITES, "rk4_steps_per_step": NSTEPS, "dt": DT,
-                       "boundary": "periodic", "sample": sample},
+            "config": {"workload": WORKLOAD, "sites": N_HEAD, "rk4_steps_per_step": NSTEPS_HEAD, "dt": DT,
+                       "boundary": BC_HEAD, "sample": sample},
             "cpu_baseline": {"value": value, "unit": "site-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "site-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -298,19 +312,19 @@ def fp32_kahan_extra(rk, torch, stream, n=1 << 27, nsteps=NSTEPS):
     return out
 
 
-def fixed_fp64_extra(rk, torch, stream, n=1 << 27, nsteps=200):
-    """Bandwidth-roofline configuration: FP64, fixed ends, N = 2^27 sites, 200 steps."""
-    h = rk.rk4_chain_create(rk.RK4_ROESSLER, rk.RK4_FP64, n, DT, rk.RK4_FIXED, None, stream)
+def periodic_fp64_extra(rk, torch, stream, n=N_SITES, nsteps=NSTEPS):
+    """The periodic FP64 chain of N = 2^24 sites, 1000 steps, autotuned blocked kernel."""
+    h = rk.rk4_chain_create(rk.RK4_ROESSLER, rk.RK4_FP64, n, DT, rk.RK4_PERIODIC, None, stream)
     try:
         st = torch.empty((n, D), dtype=torch.float64, device="cuda")
         rk.rk4_fill_uniform(st, n * D, SEED, 0, rk.RK4_FP64, stream)
         ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
-        rk.rk4_chain_set_tiling(h, 256, 4, 2)
+        tiling = rk.rk4_chain_autotune(h, st.clone(), None, ws, 16)
         rk.rk4_chain_integrate(h, st, None, ws, nsteps)  # warm-up with the timed step count (graph cached)
         el = time_integrate(rk, h, st, None, ws, nsteps, 1, torch)
         sps = n * nsteps / el
-        return {"value": sps, "unit": "site-steps/s", "N": n, "steps": nsteps, "boundary": "fixed",
-                "tiling": rk.rk4_chain_get_tiling(h), "effective_state_GBs": sps * 2 * D * 8 / 1e9,
+        return {"value": sps, "unit": "site-steps/s", "N": n, "steps": nsteps, "boundary": "periodic",
+                "tiling": tiling, "effective_state_GBs": sps * 2 * D * 8 / 1e9,
                 "fp64_pipe_frac_of_measured": sps * FP64_INST_PER_SITE_STEP / FP64_INST_PEAK}
     finally:
         rk.rk4_chain_destroy(h)
@@ -683,8 +697,8 @@ def main():
     probe = probe_peaks() if rank == 0 and not args.no_probe else None
 
     # --- the workload: one chain per rank (independent replicas, weak scaling) -------
-    n = N_SITES
-    h = rk.rk4_chain_create(rk.RK4_ROESSLER, rk.RK4_FP64, n, DT, rk.RK4_PERIODIC, None, stream)
+    n, nsteps = N_HEAD, NSTEPS_HEAD
+    h = rk.rk4_chain_create(rk.RK4_ROESSLER, rk.RK4_FP64, n, DT, rk.RK4_FIXED, None, stream)
     st = torch.empty((n, D), dtype=torch.float64, device="cuda")
     rk.rk4_fill_uniform(st, n * D, SEED, 0, rk.RK4_FP64, stream)
     ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
@@ -693,11 +707,11 @@ def main():
         tiling = rk.rk4_chain_get_tiling(h)
     else:
         tiling = rk.rk4_chain_autotune(h, st.clone(), None, ws, 16)
-    plan_launches = -(-NSTEPS // tiling["k"])
+    plan_launches = -(-nsteps // tiling["k"])
     plan_launches += plan_launches % 2  # the plan keeps an even launch count when it can
 
     def one_step():
-        rk.rk4_chain_integrate(h, st, None, ws, NSTEPS)
+        rk.rk4_chain_integrate(h, st, None, ws, nsteps)
         return rk.rk4_chain_energy(h, st, None, ws)[0]  # synchronises; checks for NaN/inf
 
     for _ in range(args.warmup):
@@ -716,17 +730,17 @@ def main():
     torch.cuda.synchronize()
     dist.barrier()
     el = dist.max_over_ranks(e0.elapsed_time(e1) / 1e3)
-    site_steps = float(n) * NSTEPS * args.steps * world
+    site_steps = float(n) * nsteps * args.steps * world
     value = site_steps / el
 
     # kernel-only timing of the blocked kernel for the roofline (same stream, events)
     reps = 2
-    el_k = time_integrate(rk, h, st, None, ws, NSTEPS, reps, torch)
+    el_k = time_integrate(rk, h, st, None, ws, nsteps, reps, torch)
     launch_s = el_k / (reps * plan_launches)
-    sps_k = n * NSTEPS * reps / el_k
+    sps_k = n * nsteps * reps / el_k
     achieved_inst = sps_k * FP64_INST_PER_SITE_STEP / 1e9  # G FP64 instructions/s
     khash = kernel_hash()
-    traffic = TRAFFIC.get((khash, f"{tiling['block']},{tiling['v']},{tiling['k']}"))
+    traffic = traffic_per_launch(khash, tiling, n)
     roofline = {"bound": "alu", "achieved": achieved_inst, "peak": FP64_INST_PEAK / 1e9,
                 "unit": "G FP64 inst/s", "frac": achieved_inst * 1e9 / FP64_INST_PEAK,
                 "traffic": traffic, "kernel": "k_blocked<double, Roessler>",
@@ -753,14 +767,14 @@ def main():
     host = torch.empty((n, D), dtype=torch.float64).pin_memory()
     host.copy_(st.cpu())
     dev2 = torch.empty_like(st)
-    rk.rk4_chain_integrate_host(h, host, None, dev2, None, ws, NSTEPS)  # warm
+    rk.rk4_chain_integrate_host(h, host, None, dev2, None, ws, nsteps)  # warm
     dist.barrier()
     t0 = time.perf_counter()
     e2e_steps = 2
     for _ in range(e2e_steps):
-        rk.rk4_chain_integrate_host(h, host, None, dev2, None, ws, NSTEPS)
+        rk.rk4_chain_integrate_host(h, host, None, dev2, None, ws, nsteps)
     el_e2e = dist.max_over_ranks(time.perf_counter() - t0)
-    e2e = {"value": float(n) * NSTEPS * e2e_steps * world / el_e2e, "unit": "site-steps/s",
+    e2e = {"value": float(n) * nsteps * e2e_steps * world / el_e2e, "unit": "site-steps/s",
            "h2d_bytes_per_step": n * D * 8, "d2h_bytes_per_step": n * D * 8,
            "api": "rk4_chain_integrate_host (pinned host state in, result out)"}
     del host, dev2
@@ -770,7 +784,7 @@ def main():
         # per-GPU side measurements add nothing to a weak-scaling line and would hold every GPU
         extras["extras"] = "skipped for n_gpus > 1 (run with one GPU)"
     elif not args.no_extras:
-        extras["fixed_fp64_2e27"] = fixed_fp64_extra(rk, torch, stream)
+        extras["periodic_fp64_2e24_1000steps"] = periodic_fp64_extra(rk, torch, stream)
         extras["fp32_kahan_2e27"] = fp32_kahan_extra(rk, torch, stream)
         extras["batch_fp64"] = batch_extra(rk, torch, stream, rk.RK4_FP64)
         extras["batch_fp32_kahan"] = batch_extra(rk, torch, stream, rk.RK4_FP32_KAHAN)
@@ -795,8 +809,8 @@ def main():
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "step_ms": {"min": step_ms[0], "median": step_ms[len(step_ms) // 2], "max": step_ms[-1]},
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sites": n, "rk4_steps_per_step": NSTEPS,
-                       "dt": DT, "boundary": "periodic", "tiling": tiling, "l2": "inputs larger than L2 (403 MB state)",
+            "config": {"workload": WORKLOAD, "sites": n, "rk4_steps_per_step": nsteps,
+                       "dt": DT, "boundary": BC_HEAD, "tiling": tiling, "l2": "inputs larger than L2 (3.2 GB state)",
                        "parallelism": f"replicas x{world}", "final_half_norm2": float(norm)},
             "roofline": roofline,
             "effective_state_GBs": value / world * 2 * D * 8 / 1e9,

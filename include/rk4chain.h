@@ -128,9 +128,10 @@ int rk4_chain_workspace_bytes(const rk4_chain *h, size_t *bytes);
 /* Total sites (sum over chains) and per-site dimension D of the handle's state. */
 int rk4_chain_shape(const rk4_chain *h, int64_t *total_sites, int *dim);
 
-/* Chooses the scheme (enum rk4_kernel).  AUTO picks BLOCKED for one chain (and for the
- * generic and heterogeneous schemes) and, for a batch, PERSISTENT -- or BLOCKED if
- * rk4_chain_autotune measured it faster.  Errors: RK4_EINVAL. */
+/* Chooses the scheme (enum rk4_kernel).  AUTO runs the scheme rk4_chain_autotune measured
+ * fastest; before any autotuning, BLOCKED for one chain (and for the generic and heterogeneous
+ * schemes) and PERSISTENT for a batch.  Setting a scheme forgets the autotuner's choice.
+ * Errors: RK4_EINVAL. */
 int rk4_chain_set_kernel(rk4_chain *h, int kernel);
 
 /* The scheme the handle will run (AUTO resolved).  Errors: RK4_EINVAL. */
@@ -174,11 +175,16 @@ int rk4_chain_set_coupling2(rk4_chain *h, double kappa2);
 int rk4_chain_set_site_params(rk4_chain *h, const void *params);
 
 /* Times the candidate tilings on the caller's buffers and keeps the fastest (the paper
- * picks G by a performance study, Sec. 3.2.1); for a batch on RK4_KERNEL_AUTO it also times
- * the persistent against the blocked scheme and keeps the faster.  The call integrates `state` (and comp)
- * forward by an unspecified number of steps: pass scratch copies.  Synchronises the stream.
- * *best (may be NULL) receives the chosen tiling.  Errors: RK4_EINVAL, RK4_ENOMEM_WS,
- * RK4_ECUDA. */
+ * picks G by a performance study, Sec. 3.2.1).  On RK4_KERNEL_AUTO it also chooses the scheme:
+ * for a batch the persistent against the blocked scheme, and for any handle the staged scheme
+ * (the paper's standard implementation, Sec. 2.2) when ws_bytes is at least the workspace that
+ * scheme needs (rk4_chain_workspace_bytes after rk4_chain_set_kernel(h, RK4_KERNEL_STAGED)):
+ * a caller that can afford the larger workspace lets the autotuner pick the unblocked scheme
+ * where it measures faster.  After a call that chose STAGED, rk4_chain_workspace_bytes reports
+ * its size, and rk4_chain_set_tiling returns the handle to the tiled schemes.  The call
+ * integrates `state` (and comp) forward by an unspecified number of steps: pass scratch copies.
+ * Synchronises the stream.  *best (may be NULL) receives the chosen tiling (the best tiled one
+ * when STAGED wins).  Errors: RK4_EINVAL, RK4_ENOMEM_WS, RK4_ECUDA. */
 int rk4_chain_autotune(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_bytes,
                        int probe_steps, rk4_tiling *best);
 
@@ -219,7 +225,8 @@ int rk4_chain_energy(rk4_chain *h, const void *state, const void *comp, void *ws
  * library, about 330 KB on every GPU that loads it, held until the process exits; batches
  * of more than 8192 chains are rejected with RK4_EINVAL.  The call allocates nothing (no
  * cudaMalloc, cudaMallocHost or cudaFree).  The first call on each device looks up the
- * array's device address, so make that first call before any stream capture.  All calls
+ * array's device address (and a call after that device's context was replaced, e.g. by
+ * cudaDeviceReset, looks it up again), so make that first call before any stream capture.  All calls
  * share the array: calls whose work overlaps on the GPU race and must be serialised by the
  * caller.  out (host) receives one value per chain.  Synchronises the stream.  Returns
  * RK4_ENONFINITE if a NaN or infinity was seen, RK4_EINVAL for bad arguments. */

@@ -1,8 +1,6 @@
 // k_blocked.cu -- temporally blocked RK4 kernel: one thread block per (chain, tile) item,
 // k steps per launch (k = 1 is the fused single-step kernel).  HET: heterogeneous chains
 // (Eq. (1) of the paper), whose per-site parameters travel with the tile.
-#include <mutex>
-
 #include "rk4_tile.cuh"
 
 namespace rk4d {
@@ -51,12 +49,8 @@ size_t blocked_smem_bytes(int model, bool fp32, int v, int block, bool het) {
 
 template <typename R, int MODEL, int V, bool KAHAN, bool HET>
 static cudaError_t launch_one(int block, const BlockedJob &job, const CoefD &cfd, cudaStream_t st) {
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_blocked<R, MODEL, V, KAHAN, HET>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    200 * 1024);
-  });
+  static PerDevice attr;
+  const cudaError_t attr_err = set_smem_limit_once(k_blocked<R, MODEL, V, KAHAN, HET>, 200 * 1024, attr);
   if (attr_err != cudaSuccess) return attr_err;
   const size_t smem = blocked_smem_bytes(MODEL, KAHAN, V, block, HET);
   Coef<R> cf = to_coef<R>(cfd, cfd.kappa);

@@ -28,7 +28,7 @@ cudaError_t launch_ghost_copy(void *state, void *comp, const GhostPair *pairs, i
   const int row_words = row_bytes / 4;
   const int64_t zone_words = ghost * row_words;
   int64_t grid = ((int64_t)npairs * zone_words + 255) / 256;
-  if (grid > 152 * 8) grid = 152 * 8;
+  if (grid > (int64_t)sm_count() * 8) grid = (int64_t)sm_count() * 8;
   k_ghost_copy<<<(unsigned)grid, 256, 0, st>>>(static_cast<uint32_t *>(state), static_cast<uint32_t *>(comp), pairs,
                                                npairs, zone_words, row_words);
   return cudaGetLastError();

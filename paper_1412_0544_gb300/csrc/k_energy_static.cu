@@ -20,7 +20,6 @@ using namespace rk4d;
 namespace {
 
 constexpr int kStaticMaxChains = 8192;
-constexpr int kMaxDevices = 64;
 
 struct StaticScratch {
   WsHeader hdr;
@@ -33,23 +32,68 @@ struct StaticScratch {
 // device address comes from cudaGetSymbolAddress (see scratch_for_current_device).
 static __device__ __align__(256) unsigned char g_energy_scratch[sizeof(StaticScratch)];
 
-std::mutex g_mu;
-StaticScratch *g_dev_ptr[kMaxDevices] = {};
+// The address of the array belongs to the device's current context: a cudaDeviceReset
+// destroys that context, and the array lives at a new address in the next one.  So the cached
+// address is keyed by the context's unique id (cuCtxGetId: ids are never reused within a
+// process), read through the driver entry points the runtime exposes.
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
 
-// Device address of the scratch array on the current device, looked up once per device.
+struct Cached {
+  bool valid;
+  unsigned long long ctx_id;
+  StaticScratch *ptr;
+};
+
+std::mutex g_mu;
+Cached g_cache[kMaxDevices] = {};
+
+// Unique id of the calling thread's current context; false when it cannot be read (no
+// current context yet, or a driver without the entry points).
+bool current_context_id(unsigned long long *id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    looked_up = true;
+    cudaDriverEntryPointQueryResult q1, q2;
+    void *f1 = nullptr, *f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+      get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+  }
+  if (!get_current || !get_id) return false;
+  void *ctx = nullptr;
+  if (get_current(&ctx) != 0 || !ctx) return false;
+  return get_id(ctx, id) == 0;
+}
+
+// Device address of the scratch array in the current device's context.  Looked up with
+// cudaGetSymbolAddress on the first call on each device and again whenever that device's
+// context has changed since (a cudaDeviceReset in between); every call when the context id
+// cannot be read.
 cudaError_t scratch_for_current_device(StaticScratch **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_dev_ptr[dev]) {
+  unsigned long long id = 0;
+  bool have_id = current_context_id(&id);
+  Cached &c = g_cache[dev];
+  if (!(c.valid && have_id && c.ctx_id == id)) {
     void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_energy_scratch);
+    e = cudaGetSymbolAddress(&p, g_energy_scratch);  // creates the primary context if needed
     if (e != cudaSuccess) return e;
-    g_dev_ptr[dev] = static_cast<StaticScratch *>(p);
+    if (!have_id) have_id = current_context_id(&id);
+    c.ptr = static_cast<StaticScratch *>(p);
+    c.ctx_id = id;
+    c.valid = have_id;
   }
-  *out = g_dev_ptr[dev];
+  *out = c.ptr;
   return cudaSuccess;
 }
 

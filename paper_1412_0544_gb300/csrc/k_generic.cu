@@ -17,7 +17,6 @@
 //   combine      inc = 0; for m with b_m != 0: inc = fma(b_m dt, k_m, inc)          (Eq. (5))
 //                FP64: y = y + inc;  FP32-Kahan: s = inc - c; t = y + s; c = (t - y) - s; y = t
 #include <algorithm>
-#include <mutex>
 
 #include "rk4_generic.cuh"
 
@@ -328,7 +327,8 @@ constexpr uint64_t kShapeDopri5 =
 
 static int64_t staged_grid(int64_t total) {
   int64_t g = (total + 255) / 256;
-  return g > 152 * 64 ? 152 * 64 : (g < 1 ? 1 : g);
+  const int64_t cap = (int64_t)sm_count() * 64;
+  return g > cap ? cap : (g < 1 ? 1 : g);
 }
 
 template <typename R, int MODEL, int RANGE, bool KAHAN>
@@ -365,12 +365,8 @@ cudaError_t launch_gen_staged_step(int model, bool fp32, int range, const GenSta
 template <typename R, int MODEL, int V, int RANGE, bool KAHAN, uint64_t SHAPE>
 static cudaError_t gen_blocked_s(int block, const BlockedJob &job, const CoefD &cfd, const TableauD &td, double dt,
                                  int H, cudaStream_t st) {
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_gen_blocked<R, MODEL, V, RANGE, KAHAN, SHAPE>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  });
+  static PerDevice attr;
+  const cudaError_t attr_err = set_smem_limit_once(k_gen_blocked<R, MODEL, V, RANGE, KAHAN, SHAPE>, 200 * 1024, attr);
   if (attr_err != cudaSuccess) return attr_err;
   if (job.ntiles <= 0) return cudaSuccess;
   const size_t smem = gen_blocked_smem_bytes(MODEL, KAHAN, V, block);

@@ -3,8 +3,6 @@
 // (chain, tile) items, then all blocks meet at a grid barrier before the next time block
 // reads what the previous one wrote.  The barrier's wait is bounded: a block that waits
 // longer than timeout_ns latches ST_TIMEOUT in the status word and the kernel returns.
-#include <mutex>
-
 #include "rk4_tile.cuh"
 
 namespace rk4d {
@@ -98,13 +96,8 @@ __global__ void __launch_bounds__(max_threads_for(V), (V >= 2 && KAHAN) ? 2 : 1)
 
 template <typename R, int MODEL, int V, bool KAHAN>
 static cudaError_t setup_attr() {
-  static std::once_flag once;
-  static cudaError_t err = cudaSuccess;
-  std::call_once(once, [] {
-    err = cudaFuncSetAttribute(k_persistent<R, MODEL, V, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               200 * 1024);
-  });
-  return err;
+  static PerDevice attr;
+  return set_smem_limit_once(k_persistent<R, MODEL, V, KAHAN>, 200 * 1024, attr);
 }
 
 template <typename R, int MODEL, int V, bool KAHAN>
@@ -134,10 +127,7 @@ static int max_grid_one(int block) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<R, MODEL, V, KAHAN>, block, smem) !=
       cudaSuccess)
     return 0;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return per_sm * sms;
+  return per_sm * sm_count();
 }
 
 #define RK4_DISPATCH_V(FN, ...)                                                                   \

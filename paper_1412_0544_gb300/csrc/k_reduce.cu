@@ -165,7 +165,7 @@ cudaError_t launch_fill_uniform(void *dst, int64_t count, uint64_t seed, uint64_
                                 cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   int64_t grid = (count + 255) / 256;
-  if (grid > 152 * 32) grid = 152 * 32;
+  if (grid > (int64_t)sm_count() * 32) grid = (int64_t)sm_count() * 32;
   if (fp32)
     k_fill_uniform<float><<<(unsigned)grid, 256, 0, st>>>(static_cast<float *>(dst), count, seed, start);
   else

@@ -76,7 +76,7 @@ static cudaError_t launch_one(int j, const StagedJob &job, const CoefD &cfd, cud
   if (job.total <= 0) return cudaSuccess;
   const int block = 256;
   int64_t grid = (job.total + block - 1) / block;
-  if (grid > 152 * 64) grid = 152 * 64;
+  if (grid > (int64_t)sm_count() * 64) grid = (int64_t)sm_count() * 64;
   k_staged<R, MODEL, KAHAN><<<(unsigned)grid, block, 0, st>>>(job, to_coef<R>(cfd, cfd.kappa), j);
   return cudaGetLastError();
 }

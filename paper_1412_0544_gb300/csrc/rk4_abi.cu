@@ -88,7 +88,7 @@ struct rk4_chain {
   // heterogeneous chain (Eq. (1)): caller-owned device array of P parameters per site
   const void *site_params = nullptr;
   unsigned gen_version = 0;  // bumped when the tableau or kappa2 changes (graph cache key)
-  int auto_kernel = RK4_KERNEL_PERSISTENT;  // scheme RK4_KERNEL_AUTO uses for a batch
+  int tuned_kernel = 0;  // scheme rk4_chain_autotune measured fastest for RK4_KERNEL_AUTO (0: not tuned)
   bool timeout_set = false;                 // RK4_OPT_TIMEOUT_NS given explicitly
   unsigned config_version = 0;              // bumped by every setter (graphs captured by callers)
 };
@@ -101,8 +101,9 @@ bool use_het(const rk4_chain *h);
 
 int effective_kernel(const rk4_chain *h) {
   if (h->kernel != RK4_KERNEL_AUTO) return h->kernel;
+  if (h->tuned_kernel != 0) return h->tuned_kernel;  // the autotuner's measured choice
   if (h->nchains == 1 || use_generic(h) || use_het(h)) return RK4_KERNEL_BLOCKED;
-  return h->auto_kernel;  // batches: persistent unless the autotuner measured the blocked scheme faster
+  return RK4_KERNEL_PERSISTENT;  // batches
 }
 
 size_t elem_bytes(const rk4_chain *h) { return h->fp32 ? 4 : 8; }
@@ -682,6 +683,7 @@ int rk4_chain_set_kernel(rk4_chain *h, int kernel) {
   if (!h || kernel < RK4_KERNEL_AUTO || kernel > RK4_KERNEL_PERSISTENT) return RK4_EINVAL;
   h->config_version++;
   h->kernel = kernel;
+  h->tuned_kernel = 0;
   return RK4_OK;
 }
 
@@ -696,6 +698,7 @@ int rk4_chain_set_tiling(rk4_chain *h, int block, int v, int k) {
   if (!tiling_valid(h, block, v, k)) return RK4_EINVAL;
   const int maxt = tiling_max_threads(h, v);
   if (maxt > 0 && block > maxt) return RK4_EINVAL;
+  if (h->tuned_kernel == RK4_KERNEL_STAGED) h->tuned_kernel = 0;  // a tiling asks for a tiled scheme
   h->tiling_auto = false;
   h->tiling.block = block;
   h->tiling.v = v;
@@ -866,19 +869,28 @@ int rk4_chain_autotune(rk4_chain *h, void *state, void *comp, void *ws, size_t w
   NvtxRange range("rk4_chain_autotune");
   int rc = check_buffers(h, state, comp, ws);
   if (rc) return rc;
-  const int kernel = effective_kernel(h);
-  if (kernel == RK4_KERNEL_STAGED) {
+  if (h->kernel == RK4_KERNEL_STAGED) {  // the one-stage-per-launch scheme has nothing to tune
     if (best) *best = h->tiling;
     return RK4_OK;
   }
-  if (ws_bytes < layout(h, kernel).total) return RK4_ENOMEM_WS;
-  // a batch left on RK4_KERNEL_AUTO: time the persistent and the blocked scheme and keep the faster
-  const bool choose_kernel = h->kernel == RK4_KERNEL_AUTO && h->nchains > 1 && !use_generic(h) && !use_het(h);
-  const int kernels[2] = {kernel, RK4_KERNEL_BLOCKED};
-  const int nkern = (choose_kernel && kernel != RK4_KERNEL_BLOCKED) ? 2 : 1;
+  // Candidate schemes.  An explicit choice is kept.  On RK4_KERNEL_AUTO: the blocked scheme, for
+  // a batch also the persistent one, and the staged scheme whenever ws is large enough for it.
+  const bool tiled_only = use_generic(h) || use_het(h);
+  const bool on_auto = h->kernel == RK4_KERNEL_AUTO;
+  std::vector<int> kernels;
+  if (!on_auto) {
+    kernels.push_back(h->kernel);
+  } else {
+    if (h->nchains > 1 && !tiled_only) kernels.push_back(RK4_KERNEL_PERSISTENT);
+    kernels.push_back(RK4_KERNEL_BLOCKED);
+  }
+  for (size_t i = 0; i < kernels.size();)  // only the schemes the caller's workspace can hold
+    if (ws_bytes < layout(h, kernels[i]).total) kernels.erase(kernels.begin() + (long)i); else ++i;
+  const bool try_staged = on_auto && ws_bytes >= layout(h, RK4_KERNEL_STAGED).total;
+  if (kernels.empty() && !try_staged) return RK4_ENOMEM_WS;
   const rk4_tiling saved = h->tiling;
-  const int saved_auto = h->auto_kernel;
-  int best_kernel = kernel;
+  const int saved_tuned = h->tuned_kernel;
+  int best_kernel = 0;
   const bool saved_graphs = h->graphs;
   h->graphs = false;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -886,64 +898,82 @@ int rk4_chain_autotune(rk4_chain *h, void *state, void *comp, void *ws, size_t w
     h->graphs = saved_graphs;
     return RK4_ECUDA;
   }
+  // Per-step time of an integration of `steps` after a warm-up of `warm`, or a negative value
+  // when the configuration fails to run.
+  auto time_steps = [&](int64_t warm, int64_t steps) -> float {
+    if (integrate_impl(h, state, comp, ws, ws_bytes, warm) != RK4_OK) return -1.f;
+    cudaEventRecord(e0, h->stream);
+    if (integrate_impl(h, state, comp, ws, ws_bytes, steps) != RK4_OK) return -1.f;
+    cudaEventRecord(e1, h->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = RK4_ECUDA;
+      return -1.f;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms / (float)steps;
+  };
   static const int blocks[] = {64, 128, 256, 512, 1024};
   static const int vs[] = {1, 2, 4, 8};
   static const int ks[] = {1, 2, 4, 8, 16};
   float best_ms = 1e30f;
   rk4_tiling best_t = saved;
+  bool have_tiling = false;
   rc = RK4_OK;
-  for (int ki = 0; ki < nkern; ++ki)
-  for (int b : blocks)
-    for (int v : vs)
-      for (int k : ks) {
-        const int kern = kernels[ki];
-        if (choose_kernel) h->auto_kernel = kern;
-        if (!tiling_valid(h, b, v, k)) continue;
-        if (b == 64 && !use_generic(h)) continue;
-        const int maxt = tiling_max_threads(h, v);
-        if (maxt <= 0 || b > maxt) continue;
-        if (kern == RK4_KERNEL_PERSISTENT && persistent_max_grid(h->model, h->fp32, v, b) <= 0) continue;
-        h->tiling.block = b;
-        h->tiling.v = v;
-        h->tiling.k = k;
-        h->tiling.G = b * v - 2 * halo(h, k);
-        const int64_t steps = ((probe_steps + 2 * k - 1) / (2 * k)) * 2 * k;  // whole, even launch count
-        if (integrate_impl(h, state, comp, ws, ws_bytes, 2 * k) != RK4_OK) continue;  // warm-up
-        cudaEventRecord(e0, h->stream);
-        if (integrate_impl(h, state, comp, ws, ws_bytes, steps) != RK4_OK) continue;
-        cudaEventRecord(e1, h->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-          rc = RK4_ECUDA;
-          break;
+  for (int kern : kernels) {
+    if (rc != RK4_OK) break;
+    if (on_auto) h->tuned_kernel = kern;
+    for (int b : blocks)
+      for (int v : vs)
+        for (int k : ks) {
+          if (rc != RK4_OK) break;
+          if (!tiling_valid(h, b, v, k)) continue;
+          if (b == 64 && !use_generic(h)) continue;
+          const int maxt = tiling_max_threads(h, v);
+          if (maxt <= 0 || b > maxt) continue;
+          if (kern == RK4_KERNEL_PERSISTENT && persistent_max_grid(h->model, h->fp32, v, b) <= 0) continue;
+          h->tiling.block = b;
+          h->tiling.v = v;
+          h->tiling.k = k;
+          h->tiling.G = b * v - 2 * halo(h, k);
+          const int64_t steps = ((probe_steps + 2 * k - 1) / (2 * k)) * 2 * k;  // whole, even launch count
+          const float per_step = time_steps(2 * k, steps);
+          if (per_step >= 0.f && per_step < best_ms) {
+            best_ms = per_step;
+            best_t = h->tiling;
+            best_kernel = kern;
+            have_tiling = true;
+          }
         }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        const float per_step = ms / (float)steps;
-        if (per_step < best_ms) {
-          best_ms = per_step;
-          best_t = h->tiling;
-          best_kernel = kern;
-        }
-      }
+  }
+  if (rc == RK4_OK && try_staged) {
+    h->tuned_kernel = RK4_KERNEL_STAGED;
+    const float per_step = time_steps(1, probe_steps);
+    if (per_step >= 0.f && per_step < best_ms) {
+      best_ms = per_step;
+      best_kernel = RK4_KERNEL_STAGED;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->graphs = saved_graphs;
   if (rc != RK4_OK || best_ms >= 1e30f) {
     h->tiling = saved;
-    h->auto_kernel = saved_auto;
+    h->tuned_kernel = saved_tuned;
     return rc != RK4_OK ? rc : RK4_ECUDA;
   }
-  if (choose_kernel) h->auto_kernel = best_kernel;
+  h->tuned_kernel = on_auto ? best_kernel : 0;
   h->config_version++;
-  h->tiling = best_t;
-  h->tiling_auto = false;
-  if (best) *best = best_t;
+  h->tiling = have_tiling ? best_t : saved;
+  h->tiling_auto = !have_tiling && h->tiling_auto;
+  if (best) *best = h->tiling;
   return RK4_OK;
 }
 
 int rk4_chain_set_tableau(rk4_chain *h, int s, const double *A, const double *b) {
   if (!h) return RK4_EINVAL;
   h->config_version++;
+  h->tuned_kernel = 0;
   if (s == 0) {  // back to the classical RK4 kernels
     h->has_tableau = false;
     h->tab = classical_rk4();
@@ -973,6 +1003,7 @@ int rk4_chain_set_tableau(rk4_chain *h, int s, const double *A, const double *b)
 int rk4_chain_set_coupling2(rk4_chain *h, double kappa2) {
   if (!h || !std::isfinite(kappa2)) return RK4_EINVAL;
   h->config_version++;
+  h->tuned_kernel = 0;
   h->kappa2 = kappa2;
   if (!h->has_tableau) h->tab = classical_rk4();
   h->gen_version++;
@@ -984,6 +1015,7 @@ int rk4_chain_set_site_params(rk4_chain *h, const void *params) {
   if (!h) return RK4_EINVAL;
   if (params && (reinterpret_cast<uintptr_t>(params) % 16) != 0) return RK4_EINVAL;
   h->config_version++;
+  h->tuned_kernel = 0;
   h->site_params = params;
   default_tiling(h);
   return RK4_OK;

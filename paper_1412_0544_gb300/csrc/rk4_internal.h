@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <mutex>
+
 namespace rk4d {
 
 // One chain of a (possibly single-chain) job.  32 bytes, stored in the workspace for batches.
@@ -147,6 +149,51 @@ size_t blocked_smem_bytes(int model, bool fp32, int v, int block, bool het = fal
 int blocked_max_threads(int model, bool fp32, int v, bool het = false);
 
 constexpr int kEnergyBlocks = 1024;  // fixed grid of the single-chain reduction (deterministic)
+
+// Per-device state of host-side set-up that CUDA scopes to the current device (a kernel's
+// shared-memory limit, a device attribute): done once for each device a process uses.
+constexpr int kMaxDevices = 64;
+struct PerDevice {
+  std::mutex m;
+  bool done[kMaxDevices] = {};
+  cudaError_t err[kMaxDevices] = {};
+  int value[kMaxDevices] = {};
+};
+
+// Raise `kernel`'s dynamic shared-memory limit to `bytes` on the current device, once per
+// device (the attribute applies only to the device that is current when it is set).
+template <typename K> inline cudaError_t set_smem_limit_once(K *kernel, int bytes, PerDevice &pd) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  std::lock_guard<std::mutex> g(pd.m);
+  if (!pd.done[dev]) {
+    pd.err[dev] = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    pd.done[dev] = true;
+  }
+  return pd.err[dev];
+}
+
+// Streaming multiprocessors of the current device (cached per device); grid-stride kernels
+// size their grids as a multiple of it.
+inline int sm_count() {
+  static PerDevice pd;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+  if (dev < 0 || dev >= kMaxDevices) {
+    int n = 0;
+    return cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0 ? n : 152;
+  }
+  std::lock_guard<std::mutex> g(pd.m);
+  if (!pd.done[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    pd.value[dev] = n;
+    pd.done[dev] = true;
+  }
+  return pd.value[dev];
+}
 
 }  // namespace rk4d
 

@@ -13,7 +13,7 @@
 #include <cstring>
 #include <cuda_runtime.h>
 
-#include "csrc/rk4_device.cuh"
+#include "paper_1412_0544_gb300/csrc/rk4_device.cuh"
 
 #define CK(x)                                                                      \
   do {                                                                             \

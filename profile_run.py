@@ -1,7 +1,7 @@
 """A short, fixed workload for profiler captures (ncu): fills a chain (or a batch) and advances
 it a given number of RK4 steps with a fixed tiling, then exits.  Nothing is timed here.
 
-    python -m paper_1412_0544_gb300.profile_run --precision fp64 --n 16777216 --steps 4 --tiling 256,4,2
+    python profile_run.py --precision fp64 --n 16777216 --steps 4 --tiling 256,4,2
 """
 from __future__ import annotations
 
@@ -9,7 +9,7 @@ import argparse
 import os
 import sys
 
-sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 
 def main():
@@ -17,6 +17,7 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--model", choices=["roessler", "harmonic"], default="roessler")
     ap.add_argument("--n", type=int, default=1 << 24)
+    ap.add_argument("--bc", choices=["periodic", "fixed"], default="periodic")
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--tiling", default="256,4,1")
     ap.add_argument("--kernel", choices=["blocked", "staged", "persistent"], default="blocked")
@@ -45,7 +46,7 @@ def main():
         h = rk.rk4_batch_create(model, prec, lengths, np.ones(args.parts), np.zeros(args.parts, dtype=np.int8), 0.01)
         total = int(lengths.sum())
     else:
-        h = rk.rk4_chain_create(model, prec, args.n, 0.01, rk.RK4_PERIODIC)
+        h = rk.rk4_chain_create(model, prec, args.n, 0.01, rk.RK4_PERIODIC if args.bc == "periodic" else rk.RK4_FIXED)
         total = args.n
     kern = {"blocked": rk.RK4_KERNEL_BLOCKED, "staged": rk.RK4_KERNEL_STAGED,
             "persistent": rk.RK4_KERNEL_PERSISTENT}[args.kernel]

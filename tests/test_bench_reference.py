@@ -1,6 +1,6 @@
 """bench.py's reference arm needs no GPU (it times the CPU oracle): its JSON line carries the
-contract's keys, its metric and unit match the GPU arm's, and under a multi-rank launch only
-rank 0 prints."""
+contract's keys, its metric and unit match the GPU arm's, under a multi-rank launch only
+rank 0 prints, and the process never loads the CUDA library (only the oracle runs there)."""
 import json
 import os
 import subprocess
@@ -9,11 +9,25 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
+# runs the reference arm in-process, then reports on stderr whether the product package was
+# imported or its shared library mapped
+_PROG = """
+import sys
+sys.argv = ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"]
+import bench
+rc = bench.main()
+maps = open("/proc/self/maps").read()
+sys.stderr.write("PRODUCT_LOADED=%d\\n" % int("paper_1412_0544_gb300" in sys.modules or "librk4chain" in maps))
+sys.exit(rc)
+"""
+
+
 def _run(env_extra):
     env = dict(os.environ, **env_extra)
-    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "3"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    r = subprocess.run([sys.executable, "-c", _PROG], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
+    assert "PRODUCT_LOADED=0" in r.stderr, r.stderr[-2000:]
     return r.stdout
 
 

@@ -1,0 +1,88 @@
+"""Energy behaviour of the GPU path on the Hamiltonian (harmonic) chain.
+
+RK4 multiplies each normal mode's energy by exactly rho(h) = 1 - h^6/72 + h^8/576 per step
+(h = omega_m dt), so the drift of the total energy after n steps is known in closed form from
+the initial state (tests/closed_form.py).  The FP64 GPU path must reproduce that drift to
+rounding.  The FP32-Kahan path carries FP32 rounding on top of it; its energy error is bounded
+by its state error: with E(y) = y^T M y / 2,
+
+    E(a) - E(b) = (a - b)^T M (a + b) / 2,   so   |E(a) - E(b)| / E(b) <= (l_max / l_min) e (2 + e),
+
+where e = |a - b| / |b| (2-norms) and l_min, l_max are the extreme eigenvalues of M: 1 and
+omega0^2 + 4 kappa for the harmonic chain (the p block is the identity; the q block is
+omega0^2 + kappa times a graph Laplacian with spectrum in [0, 4]).  The test measures e against
+the FP64 oracle and asserts the FP32 energy drift within that bound of RK4's exact drift.
+"""
+import numpy as np
+import pytest
+
+import chain_inputs as ci
+import closed_form as cf
+import oracle
+from tolerances import FP32_KAHAN_TOL
+
+pytestmark = pytest.mark.gpu
+
+PER, FIX = 0, 1
+HAR = 1
+KAPPA, OMEGA0, DT, T = 1.0, 1.0, 0.01, 1000
+
+
+@pytest.fixture(scope="module")
+def rk():
+    import torch
+    import paper_1412_0544_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+def _run(rk, y0, precision, bc):
+    """Integrate on the GPU; returns (state - compensation as float64, E0, E_final) with both
+    energies from the library's FP64 reduction."""
+    import torch
+    fp32 = precision == rk.RK4_FP32_KAHAN
+    h = rk.rk4_chain_create(HAR, precision, y0.shape[0], DT, bc, dict(kappa=KAPPA, omega0=OMEGA0))
+    try:
+        st = torch.from_numpy(np.ascontiguousarray(y0)).cuda()
+        cp = torch.zeros_like(st) if fp32 else None
+        ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+        e0 = rk.rk4_chain_energy(h, st, cp, ws)[0]
+        rk.rk4_chain_integrate(h, st, cp, ws, T)
+        e1 = rk.rk4_chain_energy(h, st, cp, ws)[0]
+        out = st.double() - (cp.double() if fp32 else 0.0)
+        return out.cpu().numpy(), e0, e1
+    finally:
+        rk.rk4_chain_destroy(h)
+
+
+@pytest.mark.parametrize("bc", [PER, FIX])
+def test_fp64_energy_drift_equals_rk4_modal_drift(rk, bc):
+    y0 = ci.uniform_state(1 << 16, 2, seed=500 + bc)
+    _, e0, e1 = _run(rk, y0, rk.RK4_FP64, bc)
+    e0_modal = float(np.sum(cf.modal_energy(y0, bc, KAPPA, OMEGA0)))
+    pred = cf.rk4_energy(y0, bc, KAPPA, OMEGA0, DT, T) / e0_modal - 1.0
+    drift = e1 / e0 - 1.0
+    print(f"harmonic FP64 bc={bc}: drift {drift:.9e}, RK4 modal prediction {pred:.9e}")
+    assert abs(e0 - e0_modal) <= 1e-12 * e0_modal
+    assert abs(drift - pred) <= 1e-12
+    assert pred < 0  # RK4 loses energy in every mode (rho(h) < 1 for 0 < h < 2.8)
+
+
+@pytest.mark.parametrize("bc", [PER, FIX])
+def test_fp32_kahan_energy_drift_bounded_by_state_error(rk, bc):
+    y32 = ci.uniform_state(1 << 16, 2, seed=510 + bc).astype(np.float32)
+    y0 = y32.astype(np.float64)
+    got, e0, e1 = _run(rk, y32, rk.RK4_FP32_KAHAN, bc)
+    ref = oracle.rk4_integrate(y0, HAR, bc, DT, T, oracle.params(kappa=KAPPA, omega0=OMEGA0))
+    e2 = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    e0_modal = float(np.sum(cf.modal_energy(y0, bc, KAPPA, OMEGA0)))
+    pred = cf.rk4_energy(y0, bc, KAPPA, OMEGA0, DT, T) / e0_modal - 1.0
+    drift = e1 / e0 - 1.0
+    cond = (OMEGA0 ** 2 + 4.0 * KAPPA) / min(1.0, OMEGA0 ** 2)
+    bound = cond * e2 * (2.0 + e2) * (1.0 + pred) + 1e-12
+    print(f"harmonic FP32-Kahan bc={bc}: drift {drift:.3e}, RK4 modal prediction {pred:.3e}, "
+          f"state error (2-norm) {e2:.2e}, bound on |drift - prediction| {bound:.2e}, "
+          f"ratio to the modal drift {abs(drift - pred) / abs(pred):.1f}")
+    assert abs(e0 - e0_modal) <= 1e-12 * e0_modal  # the start values are exact in both precisions
+    assert e2 <= FP32_KAHAN_TOL
+    assert abs(drift - pred) <= bound

@@ -13,6 +13,7 @@ import pytest
 import chain_inputs as ci
 import closed_form as cf
 import oracle
+from tolerances import FP32_KAHAN_TOL
 
 pytestmark = pytest.mark.gpu
 
@@ -70,9 +71,11 @@ def sample_sites(n, G):
     return sorted(x for x in s if 0 <= x < n)
 
 
-def run_chain(rk, n, bc, prec, T, tiling=None, autotune=False):
+def run_chain(rk, n, bc, prec, T, tiling=None, autotune=False, kernel=None):
     import torch
     h = rk.rk4_chain_create(rk.RK4_ROESSLER, prec, n, 0.01, bc)
+    if kernel is not None:
+        rk.rk4_chain_set_kernel(h, kernel)
     dt = torch.float64 if prec == rk.RK4_FP64 else torch.float32
     st = torch.empty((n, 3), dtype=dt, device="cuda")
     rk.rk4_fill_uniform(st, n * 3, SEED, 0, prec)
@@ -103,8 +106,10 @@ def test_bench_workload_fp64_2e24_1000_steps(rk):
 
 
 def test_fixed_fp64_2e27_200_steps(rk):
+    """The benchmark's workload and launch configuration (fixed ends, N = 2^27, 200 steps,
+    autotuned tiling), sampled against the oracle."""
     n, T = 1 << 27, 200
-    st, _, til = run_chain(rk, n, rk.RK4_FIXED, rk.RK4_FP64, T, tiling=(256, 4, 2))
+    st, _, til = run_chain(rk, n, rk.RK4_FIXED, rk.RK4_FP64, T, autotune=True)
     sites = sample_sites(n, til["G"])
     got = st[sites].cpu().numpy()
     ref = np.array([cone_oracle(i, n, T, oracle.FIXED) for i in sites])
@@ -134,7 +139,7 @@ def test_fp32_kahan_2e27_1000_steps(rk):
     ref = np.array([cone_oracle(i, n, T, oracle.PERIODIC, dtype=np.float32) for i in sites])
     err = cf.rel_inf(got, ref)
     print(f"N=2^27 FP32-Kahan 1000 steps: sampled rel err vs FP64 oracle {err:.2e}")
-    assert err <= 1e-5
+    assert err <= FP32_KAHAN_TOL
 
 
 def test_batch_4096_chains_1000_steps(rk):
@@ -165,5 +170,53 @@ def test_batch_4096_chains_1000_steps(rk):
             if cp is not None:
                 got = got - cp[a:b].double()
             err = cf.rel_inf(got.cpu().numpy(), ref)
-            assert err <= (1e-12 if prec == rk.RK4_FP64 else 1e-5), (c, int(lengths[c]), err)
+            assert err <= (1e-12 if prec == rk.RK4_FP64 else FP32_KAHAN_TOL), (c, int(lengths[c]), err)
         rk.rk4_chain_destroy(h)
+
+
+# Tilings of the full-size bitwise check: for each tile width W = block x v, one shape with the
+# per-thread shared-memory exchange (4 or 8 sites per thread) and one with the warp-shuffle
+# exchange (1 or 2 sites per thread), where the kernels are compiled for it.
+FULLSIZE_SHAPES = {256: [(64, 4), (256, 1)], 512: [(128, 4), (256, 2)], 1024: [(256, 4), (512, 2)],
+                   2048: [(512, 4), (256, 8)]}
+
+
+def test_blocked_bitwise_equals_staged_2e24_1000_steps(rk):
+    """Sec. 2.3: granularity with overlap gives the cluster's exact result.  At N = 2^24 and
+    1000 steps, every tiling of the sweep (W = 256 .. 2048 sites per tile, k = 1, 2, 4, 8 steps
+    per launch), the autotuned pick and the persistent kernel all produce the one-stage-per-launch
+    kernel's state bit for bit."""
+    import torch
+    n, T = 1 << 24, 1000
+    ref, _, _ = run_chain(rk, n, rk.RK4_PERIODIC, rk.RK4_FP64, T, kernel=rk.RK4_KERNEL_STAGED)
+    checked = []
+    for W, shapes in FULLSIZE_SHAPES.items():
+        for block, v in shapes:
+            for k in (1, 2, 4, 8):
+                st, _, _ = run_chain(rk, n, rk.RK4_PERIODIC, rk.RK4_FP64, T, tiling=(block, v, k),
+                                     kernel=rk.RK4_KERNEL_BLOCKED)
+                assert torch.equal(st, ref), (block, v, k)
+                checked.append((block, v, k))
+                del st
+    st, _, til = run_chain(rk, n, rk.RK4_PERIODIC, rk.RK4_FP64, T, autotune=True)
+    assert torch.equal(st, ref), til
+    del st
+    st, _, til = run_chain(rk, n, rk.RK4_PERIODIC, rk.RK4_FP64, T, tiling=(256, 4, 4),
+                           kernel=rk.RK4_KERNEL_PERSISTENT)
+    assert torch.equal(st, ref), ("persistent", til)
+    assert len(checked) == 32
+
+
+def test_fp32_kahan_bitwise_equals_staged_2e24_1000_steps(rk):
+    """The same for the FP32-Kahan path (state and compensation), on the tilings the autotuner
+    picks from (k up to 16) and the persistent kernel."""
+    import torch
+    n, T = 1 << 24, 1000
+    ref, cref, _ = run_chain(rk, n, rk.RK4_PERIODIC, rk.RK4_FP32_KAHAN, T, kernel=rk.RK4_KERNEL_STAGED)
+    for tiling in [(256, 4, 1), (256, 4, 4), (512, 4, 16), (128, 8, 16), (256, 2, 8), (1024, 1, 2)]:
+        st, cp, _ = run_chain(rk, n, rk.RK4_PERIODIC, rk.RK4_FP32_KAHAN, T, tiling=tiling,
+                              kernel=rk.RK4_KERNEL_BLOCKED)
+        assert torch.equal(st, ref) and torch.equal(cp, cref), tiling
+    st, cp, til = run_chain(rk, n, rk.RK4_PERIODIC, rk.RK4_FP32_KAHAN, T, tiling=(256, 4, 8),
+                            kernel=rk.RK4_KERNEL_PERSISTENT)
+    assert torch.equal(st, ref) and torch.equal(cp, cref), ("persistent", til)

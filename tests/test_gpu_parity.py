@@ -15,6 +15,7 @@ import pytest
 import chain_inputs as ci
 import closed_form as cf
 import oracle
+from tolerances import FP32_KAHAN_TOL
 
 pytestmark = pytest.mark.gpu
 
@@ -215,7 +216,7 @@ def test_fp32_kahan_bitwise_and_error(rk, gh):
     ref = oracle.rk4_integrate(y0.astype(np.float64), ROE, PER, 0.01, 1000)
     err = rel(st - c_st, ref)
     print(f"FP32-Kahan Roessler N=65536, 1000 steps: rel err vs FP64 oracle {err:.3e}")
-    assert err <= 1e-4
+    assert err <= FP32_KAHAN_TOL
 
 
 def test_fp32_kahan_harmonic_error(rk, gh):
@@ -400,3 +401,36 @@ def test_checkpoint_resume_bitwise(rk, tmp_path):
     rk.rk4_chain_destroy(h)
     assert meta["nstep"] == 25 and t_resumed == t_full
     assert np.array_equal(st2.cpu().numpy(), full[0]) and np.array_equal(cp2.cpu().numpy(), full[1])
+
+
+def test_autotune_considers_staged_scheme_when_workspace_allows(rk, gh):
+    """With a workspace large enough for the staged scheme, the autotuner also times it and keeps
+    whichever scheme is faster; with the blocked scheme's workspace it keeps a tiled scheme.
+    Either way the result equals the staged kernel's bit for bit."""
+    import torch
+    n, T = 1 << 20, 37
+    y0 = ci.uniform_state(n, 3, seed=77)
+    ref = gh.gpu_run(y0, nsteps=T, kernel=rk.RK4_KERNEL_STAGED)
+    h = rk.rk4_chain_create(ROE, rk.RK4_FP64, n, 0.01, PER)
+    try:
+        small = rk.rk4_chain_workspace_bytes(h)
+        rk.rk4_chain_set_kernel(h, rk.RK4_KERNEL_STAGED)
+        large = rk.rk4_chain_workspace_bytes(h)
+        rk.rk4_chain_set_kernel(h, rk.RK4_KERNEL_AUTO)
+        assert large > small
+        for nbytes, allowed in ((small, {rk.RK4_KERNEL_BLOCKED}),
+                                (large, {rk.RK4_KERNEL_BLOCKED, rk.RK4_KERNEL_STAGED})):
+            ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            st = gh.to_dev(y0, torch.float64)
+            rk.rk4_chain_autotune(h, st.clone(), None, ws, 8)
+            kern = rk.rk4_chain_get_kernel(h)
+            assert kern in allowed, kern
+            assert rk.rk4_chain_workspace_bytes(h) <= nbytes
+            rk.rk4_chain_integrate(h, st, None, ws, T)
+            assert np.array_equal(st.cpu().numpy(), ref), kern
+            print(f"autotune with {nbytes} B of workspace: kernel {kern}")
+            del ws, st
+        rk.rk4_chain_set_tiling(h, 256, 4, 1)  # an explicit tiling returns to the tiled scheme
+        assert rk.rk4_chain_get_kernel(h) == rk.RK4_KERNEL_BLOCKED
+    finally:
+        rk.rk4_chain_destroy(h)

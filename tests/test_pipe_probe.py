@@ -3,7 +3,7 @@ its packed f32x2 FMA rounds every half exactly like the scalar FMA, its rates ar
 the RK4 arithmetic on register-resident sites runs no faster than the pipe it issues to."""
 import pytest
 
-from paper_1412_0544_gb300 import pipe_probe
+import pipe_probe
 
 
 def test_probe_compiles():

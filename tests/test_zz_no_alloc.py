@@ -33,23 +33,46 @@ def _agree(a, b):
     return np.all(np.abs(a - b) <= TOL * np.maximum(np.abs(b), 1e-300))
 
 
-def test_static_energy_matches_workspace_energy_single_chain(rk):
+def _static_no_alloc(rk, h, st, cp, check):
+    """One rk4_chain_energy_static call; with `check`, the device's free memory is read right
+    before and right after it (the device idle both times) and must not change.  Only calls
+    after the first are checked: the first call on a device looks up the scratch array's
+    address, and with lazy module loading that lookup is what brings the array (compiled into
+    the library, not allocated by the call) onto the device."""
     import torch
-    for model, D, bc in ((rk.RK4_HARMONIC, 2, rk.RK4_FIXED), (rk.RK4_ROESSLER, 3, rk.RK4_PERIODIC)):
-        h = rk.rk4_chain_create(model, rk.RK4_FP64, 100003, 0.01, bc, dict(kappa=1.1, omega0=0.9))
-        try:
-            ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
-            for call, seed in enumerate((5, 6)):  # two calls in a row, different states
-                st = _dev(ci.uniform_state(100003, D, seed=seed), torch.float64)
-                ref = rk.rk4_chain_energy(h, st, None, ws)
-                if call == 1:
-                    free_before = torch.cuda.mem_get_info()[0]
-                got = rk.rk4_chain_energy_static(h, st, None)
-                if call == 1:
-                    assert torch.cuda.mem_get_info()[0] == free_before
-                assert _agree(got, ref), (got, ref)
-        finally:
-            rk.rk4_chain_destroy(h)
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    got = rk.rk4_chain_energy_static(h, st, cp)
+    torch.cuda.synchronize()
+    if check:
+        assert torch.cuda.mem_get_info()[0] == free_before
+    return got
+
+
+# (model, precision, D, boundary, second-neighbour coupling): the FP64 and FP32-Kahan
+# reductions of both models, and the harmonic energy with second-neighbour bonds
+SINGLE_CASES = [(0, 0, 3, 0, 0.0), (1, 0, 2, 1, 0.0), (0, 1, 3, 1, 0.0), (1, 1, 2, 0, 0.0), (1, 0, 2, 0, 0.45),
+                (1, 1, 2, 1, 0.45)]
+
+
+@pytest.mark.parametrize("model,prec,D,bc,kappa2", SINGLE_CASES)
+def test_static_energy_matches_workspace_energy_single_chain(rk, model, prec, D, bc, kappa2):
+    import torch
+    n = 100003
+    dtype = torch.float32 if prec == rk.RK4_FP32_KAHAN else torch.float64
+    h = rk.rk4_chain_create(model, prec, n, 0.01, bc, dict(kappa=1.1, omega0=0.9))
+    try:
+        if kappa2:
+            rk.rk4_chain_set_coupling2(h, kappa2)
+        ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+        for call, seed in enumerate((5, 6)):  # two calls in a row, different states
+            st = _dev(ci.uniform_state(n, D, seed=seed + 10 * prec), dtype)
+            cp = (st * 1e-8).contiguous() if prec == rk.RK4_FP32_KAHAN else None
+            ref = rk.rk4_chain_energy(h, st, cp, ws)
+            got = _static_no_alloc(rk, h, st, cp, check=call == 1)
+            assert _agree(got, ref), (got, ref)
+    finally:
+        rk.rk4_chain_destroy(h)
 
 
 def test_static_energy_matches_workspace_energy_batch_fp32(rk):
@@ -71,8 +94,22 @@ def test_static_energy_matches_workspace_energy_batch_fp32(rk):
         rk.rk4_chain_destroy(h)
 
 
-def test_static_energy_rejects_batches_beyond_its_scratch(rk):
+def test_static_energy_largest_batch_and_rejection_beyond(rk):
+    """8192 chains, the scratch array's limit, are reduced (twice, matching the workspace
+    reduction); 8193 are rejected with RK4_EINVAL before anything is enqueued."""
     import torch
+    lengths, kappa, bcs = ci.batch_spec(8192, seed=9, nmin=1, nmax=300)
+    total = int(lengths.sum())
+    h = rk.rk4_batch_create(rk.RK4_HARMONIC, rk.RK4_FP64, lengths, kappa, bcs, 0.01)
+    try:
+        ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+        for call, seed in enumerate((10, 11)):
+            st = _dev(ci.uniform_state(total, 2, seed=seed), torch.float64)
+            ref = rk.rk4_chain_energy(h, st, None, ws)
+            got = _static_no_alloc(rk, h, st, None, check=call == 1)
+            assert got.shape == (8192,) and _agree(got, ref)
+    finally:
+        rk.rk4_chain_destroy(h)
     h = rk.rk4_batch_create(rk.RK4_ROESSLER, rk.RK4_FP64, np.full(8193, 2), np.ones(8193), np.zeros(8193), 0.01)
     try:
         st = torch.zeros((8193 * 2, 3), dtype=torch.float64, device="cuda")
