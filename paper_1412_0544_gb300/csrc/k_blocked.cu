@@ -23,6 +23,14 @@ __global__ void __launch_bounds__(BlockedBounds<MODEL, V, KAHAN, HET>::threads,
     k_blocked(BlockedJob job, Coef<R> cf) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t item = blockIdx.x;
+  if constexpr (!HET) {
+    if (job.nchains > 1 && job.packed) {
+      batch_item<R, MODEL, V, KAHAN, false>(static_cast<const R *>(job.in), static_cast<R *>(job.out),
+                                            static_cast<const R *>(job.cin), static_cast<R *>(job.cout), job.chains,
+                                            job.nchains, job.bt, item, job.K, job.G, cf, smem, job.total, job.hdr);
+      return;
+    }
+  }
   ChainDesc ch;
   int64_t tile = item;
   Coef<R> c = cf;

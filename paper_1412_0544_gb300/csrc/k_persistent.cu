@@ -57,7 +57,6 @@ __global__ void __launch_bounds__(max_threads_for(V), (V >= 2 && KAHAN) ? 2 : 1)
     const int K = job.kval[ki];
     const int G = job.Gval[ki];
     const int64_t ntiles = job.ntiles[ki];
-    const int32_t *prefix = job.tile_prefix ? job.tile_prefix + (size_t)ki * (job.nchains + 1) : nullptr;
     const R *in = static_cast<const R *>((t & 1) ? job.bufB : job.bufA);
     R *out = static_cast<R *>((t & 1) ? job.bufA : job.bufB);
     const R *cin = static_cast<const R *>((t & 1) ? job.cB : job.cA);
@@ -71,19 +70,12 @@ __global__ void __launch_bounds__(max_threads_for(V), (V >= 2 && KAHAN) ? 2 : 1)
     if (threadIdx.x == 0) s_item = (long long)atomicAdd(ctr, 1ull);
     __syncthreads();
     for (int64_t item = s_item; item < ntiles;) {
-      ChainDesc ch;
-      int64_t tile = item;
-      Coef<R> c = cf;
-      if (job.nchains == 1) {
-        ch = job.one;
-      } else {
-        const int ci = find_chain(prefix, job.nchains, item);
-        ch = job.chains[ci];
-        tile = item - prefix[ci];
-        c.kappa = (R)ch.kappa;
-      }
-      tile_item<R, MODEL, V, KAHAN, true>(in, out, cin, cout, ch, tile, K, G, c, smem, job.total, job.hdr);
-      // tile_item ends with a barrier, so every thread has read s_item before it is rewritten
+      if (job.nchains == 1)
+        tile_item<R, MODEL, V, KAHAN, true>(in, out, cin, cout, job.one, item, K, G, cf, smem, job.total, job.hdr);
+      else
+        batch_item<R, MODEL, V, KAHAN, true>(in, out, cin, cout, job.chains, job.nchains, job.bt[ki], item, K, G, cf,
+                                             smem, job.total, job.hdr);
+      // both end with a barrier, so every thread has read s_item before it is rewritten
       if (threadIdx.x == 0) s_item = (long long)atomicAdd(ctr, 1ull);
       __syncthreads();
       item = s_item;

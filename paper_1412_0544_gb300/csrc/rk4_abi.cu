@@ -71,12 +71,17 @@ struct rk4_chain {
   int64_t nstep = 0;
   bool graphs = true;
   long long timeout_ns = 2000000000LL;
-  // pinned host staging: chain table followed by kMaxDistinctK tile-prefix arrays
+  // pinned host staging: chain table followed by kMaxDistinctK per-k tile tables (see
+  // ktable_bytes), in the same relative layout as in the workspace
   void *h_tables = nullptr;
   size_t tables_bytes = 0;
-  std::vector<int> tables_k;  // the k values the prefix arrays currently describe
+  std::vector<int> tables_k;  // the k values the tile tables currently describe
   int tables_W = 0;           // and the tile width they were computed for
-  int tables_halo = 0;        // and the halo per step
+  int tables_v = 0;           // the sites per thread (packed segments are aligned to it)
+  int tables_halo = 0;        // the halo per step
+  int tables_packed = -1;     // and whether they are packed (see packed_batch)
+  int64_t nfull[kMaxDistinctK] = {};    // packed batches: full tiles per k slot
+  int64_t npacked[kMaxDistinctK] = {};  // and packed tiles
   double *h_out = nullptr;    // pinned: reduction results (nchains doubles)
   int *h_status = nullptr;    // pinned: status word read-back
   GraphKey gkey;
@@ -148,6 +153,13 @@ TableauD classical_rk4() {
   return t;
 }
 
+// Bytes of one k slot of the batch tile tables: the first-tile prefix (nchains + 1 entries;
+// full tiles when packed, all tiles otherwise), the packed tiles' first-segment prefix
+// (nchains + 1) and the segments (at most one per chain).
+size_t ktable_bytes(int nchains) {
+  return align_up(sizeof(int32_t) * (size_t)(nchains + 1)) * 2 + align_up(sizeof(SegDesc) * (size_t)nchains);
+}
+
 WsLayout layout(const rk4_chain *h, int kernel) {
   WsLayout L{};
   size_t o = 0;
@@ -160,7 +172,7 @@ WsLayout layout(const rk4_chain *h, int kernel) {
   L.partials = take(sizeof(double) * kEnergyBlocks);
   L.result = take(sizeof(double) * (size_t)h->nchains);
   L.chains = take(h->nchains > 1 ? sizeof(ChainDesc) * (size_t)h->nchains : 0);
-  L.prefix = take(h->nchains > 1 ? sizeof(int32_t) * (size_t)(h->nchains + 1) * kMaxDistinctK : 0);
+  L.prefix = take(h->nchains > 1 ? ktable_bytes(h->nchains) * kMaxDistinctK : 0);
   const size_t sz = (size_t)h->total * (size_t)h->D * elem_bytes(h);
   L.state = L.comp = L.u0 = L.u1 = L.acc = 0;
   if (kernel == RK4_KERNEL_STAGED && use_generic(h)) {
@@ -243,6 +255,12 @@ int64_t tiles_for(const rk4_chain *h, int G) {
   return t;
 }
 
+// Batches on the classical homogeneous kernels (blocked and persistent) pack the chains' last
+// partial pieces into shared tiles; the generic and heterogeneous kernels give every chain
+// whole tiles of its own.
+bool packed_batch(const rk4_chain *h) { return h->nchains > 1 && !use_generic(h) && !use_het(h); }
+
+
 Plan make_plan(int64_t nsteps, int K) {
   Plan P;
   P.kval.push_back(K);
@@ -287,8 +305,7 @@ cudaError_t ensure_pinned(rk4_chain *h) {
   if (h->nchains > 1 && !h->h_tables) {
     // same relative layout as the workspace: chain table, then the prefix arrays at the next
     // 256-byte boundary
-    h->tables_bytes = align_up(sizeof(ChainDesc) * (size_t)h->nchains) +
-                      sizeof(int32_t) * (size_t)(h->nchains + 1) * kMaxDistinctK;
+    h->tables_bytes = align_up(sizeof(ChainDesc) * (size_t)h->nchains) + ktable_bytes(h->nchains) * kMaxDistinctK;
     cudaError_t e = cudaMallocHost(&h->h_tables, h->tables_bytes);
     if (e != cudaSuccess) return e;
     std::memcpy(h->h_tables, h->chains.data(), sizeof(ChainDesc) * (size_t)h->nchains);
@@ -296,27 +313,117 @@ cudaError_t ensure_pinned(rk4_chain *h) {
   return cudaSuccess;
 }
 
-// Fill the pinned tile-prefix arrays for the plan's k values (waits for earlier uses first).
+// The batch tile tables of k slot `ki` (pinned host copy, same layout as the workspace).
+struct KTables {
+  int32_t *prefix, *pack_prefix;
+  SegDesc *segs;
+};
+KTables host_ktables(rk4_chain *h, int ki) {
+  char *p = static_cast<char *>(h->h_tables) + align_up(sizeof(ChainDesc) * (size_t)h->nchains) +
+            ktable_bytes(h->nchains) * (size_t)ki;
+  const size_t pre = align_up(sizeof(int32_t) * (size_t)(h->nchains + 1));
+  return {reinterpret_cast<int32_t *>(p), reinterpret_cast<int32_t *>(p + pre), reinterpret_cast<SegDesc *>(p + 2 * pre)};
+}
+BatchTiles dev_ktables(const rk4_chain *h, const char *ws, const WsLayout &L, int ki) {
+  const char *p = ws + L.prefix + ktable_bytes(h->nchains) * (size_t)ki;
+  const size_t pre = align_up(sizeof(int32_t) * (size_t)(h->nchains + 1));
+  BatchTiles bt{};
+  bt.full_prefix = reinterpret_cast<const int32_t *>(p);
+  bt.pack_prefix = reinterpret_cast<const int32_t *>(p + pre);
+  bt.segs = reinterpret_cast<const SegDesc *>(p + 2 * pre);
+  bt.nfull = h->nfull[ki];
+  bt.npacked = h->npacked[ki];
+  return bt;
+}
+
+// Pack the segments of one k slot into tiles of W slots: each chain's last partial piece of
+// cnt = n mod G interior sites (the whole chain when n < G) needs a window of
+// L = H + cnt + H slots, rounded up to a multiple of v.  Best fit in decreasing order of L (the
+// fullest tile that still has room, ties to the earliest opened), which leaves little unused
+// room.  Returns the number of packed tiles; fills pack_prefix and segs in tile order.
+int64_t pack_segments(const rk4_chain *h, int G, int H, int W, int v, int32_t *pack_prefix, SegDesc *segs) {
+  struct Piece {
+    int chain, cnt, L;
+  };
+  std::vector<Piece> pieces;
+  for (int c = 0; c < h->nchains; ++c) {
+    const int cnt = (int)(h->chains[c].n % G);
+    if (cnt == 0) continue;
+    const int L = (cnt + 2 * H + v - 1) / v * v;
+    pieces.push_back({c, cnt, L});
+  }
+  std::stable_sort(pieces.begin(), pieces.end(), [](const Piece &a, const Piece &b) { return a.L > b.L; });
+  // open tiles by free room (in units of v slots): the tiles of each room size, earliest first
+  const int units = W / v;
+  std::vector<std::vector<int>> by_room(units + 1);
+  std::vector<int> room;                       // free slots of each tile
+  std::vector<std::vector<int>> members;       // pieces of each tile, in slot order
+  for (int i = 0; i < (int)pieces.size(); ++i) {
+    const int need = pieces[i].L / v;
+    int t = -1;
+    for (int r = need; r <= units && t < 0; ++r)
+      if (!by_room[r].empty()) {
+        // earliest-opened tile of this room size (tiles are only appended in opening order)
+        auto &bucket = by_room[r];
+        auto it = std::min_element(bucket.begin(), bucket.end());
+        t = *it;
+        bucket.erase(it);
+      }
+    if (t < 0) {
+      t = (int)room.size();
+      room.push_back(units);
+      members.emplace_back();
+    }
+    members[t].push_back(i);
+    room[t] -= need;
+    by_room[room[t]].push_back(t);
+  }
+  int32_t next = 0;
+  for (size_t t = 0; t < members.size(); ++t) {
+    pack_prefix[t] = next;
+    int o = 0;
+    for (int i : members[t]) {
+      const Piece &p = pieces[i];
+      SegDesc &sd = segs[next++];
+      sd.chain = p.chain;
+      sd.cnt = p.cnt;
+      sd.L = p.L;
+      sd.o = o;
+      sd.g0 = h->chains[p.chain].n - p.cnt;
+      o += p.L;
+    }
+  }
+  pack_prefix[members.size()] = next;
+  return (int64_t)members.size();
+}
+
+// Fill the pinned batch tile tables for the plan's k values (waits for earlier uses first).
 cudaError_t prepare_tables(rk4_chain *h, const std::vector<int> &kval, int W) {
   if (h->nchains == 1) return cudaSuccess;
-  if (h->tables_k == kval && h->tables_W == W && h->tables_halo == halo(h, 1)) return cudaSuccess;
+  const int packed = packed_batch(h) ? 1 : 0;
+  if (h->tables_k == kval && h->tables_W == W && h->tables_v == h->tiling.v && h->tables_halo == halo(h, 1) &&
+      h->tables_packed == packed)
+    return cudaSuccess;
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return e;
-  int32_t *pre = reinterpret_cast<int32_t *>(static_cast<char *>(h->h_tables) +
-                                             align_up(sizeof(ChainDesc) * (size_t)h->nchains));
   for (size_t i = 0; i < kval.size(); ++i) {
-    const int G = W - 2 * halo(h, kval[i]);
+    const int H = halo(h, kval[i]);
+    const int G = W - 2 * H;
+    KTables t = host_ktables(h, (int)i);
     int64_t acc = 0;
-    int32_t *p = pre + i * (size_t)(h->nchains + 1);
     for (int c = 0; c < h->nchains; ++c) {
-      p[c] = (int32_t)acc;
-      acc += (h->chains[c].n + G - 1) / G;
+      t.prefix[c] = (int32_t)acc;
+      acc += packed ? h->chains[c].n / G : (h->chains[c].n + G - 1) / G;
     }
-    p[h->nchains] = (int32_t)acc;
+    t.prefix[h->nchains] = (int32_t)acc;
+    h->nfull[i] = acc;
+    h->npacked[i] = packed ? pack_segments(h, G, H, W, h->tiling.v, t.pack_prefix, t.segs) : 0;
   }
   h->tables_k = kval;
   h->tables_W = W;
+  h->tables_v = h->tiling.v;
   h->tables_halo = halo(h, 1);
+  h->tables_packed = packed;
   return cudaSuccess;
 }
 
@@ -390,15 +497,20 @@ cudaError_t enqueue_integrate(rk4_chain *h, int kernel, void *state, void *comp,
     j.sp = h->site_params;
     j.hdr = reinterpret_cast<WsHeader *>(ws + L.hdr);
     j.total = h->total;
-    const int32_t *pre = h->nchains > 1 ? reinterpret_cast<const int32_t *>(ws + L.prefix) : nullptr;
+    j.packed = packed_batch(h) ? 1 : 0;
     for (int64_t i = 0; i < P.count(); ++i) {
       const int k = P.k_at(i);
       int ki = 0;
       while (P.kval[ki] != k) ++ki;
       j.K = k;
       j.G = W - 2 * halo(h, k);
-      j.ntiles = tiles_for(h, j.G);
-      j.tile_prefix = pre ? pre + (size_t)ki * (h->nchains + 1) : nullptr;
+      if (h->nchains > 1) {
+        j.bt = dev_ktables(h, ws, L, ki);
+        j.tile_prefix = j.bt.full_prefix;
+        j.ntiles = j.bt.nfull + j.bt.npacked;
+      } else {
+        j.ntiles = tiles_for(h, j.G);
+      }
       const bool even = (i % 2) == 0;
       j.in = even ? state : wsS;
       j.out = even ? wsS : state;
@@ -420,13 +532,17 @@ cudaError_t enqueue_integrate(rk4_chain *h, int kernel, void *state, void *comp,
     j.nchains = h->nchains;
     j.one = h->chains[0];
     j.chains = dev_chains(h, ws, L);
-    j.tile_prefix = h->nchains > 1 ? reinterpret_cast<const int32_t *>(ws + L.prefix) : nullptr;
     j.nk = (int)P.kval.size();
     int64_t maxtiles = 0;
     for (int i = 0; i < j.nk; ++i) {
       j.kval[i] = P.kval[i];
       j.Gval[i] = W - 8 * P.kval[i];
-      j.ntiles[i] = tiles_for(h, j.Gval[i]);
+      if (h->nchains > 1) {
+        j.bt[i] = dev_ktables(h, ws, L, i);
+        j.ntiles[i] = j.bt[i].nfull + j.bt[i].npacked;
+      } else {
+        j.ntiles[i] = tiles_for(h, j.Gval[i]);
+      }
       maxtiles = std::max(maxtiles, j.ntiles[i]);
     }
     j.nmain = P.nmain;
@@ -841,12 +957,16 @@ int rk4_debug_barrier_timeout(rk4_chain *h, void *state, void *comp, void *ws, s
   j.nchains = h->nchains;
   j.one = h->chains[0];
   j.chains = dev_chains(h, w, L);
-  j.tile_prefix = h->nchains > 1 ? reinterpret_cast<const int32_t *>(w + L.prefix) : nullptr;
   j.nk = 1;
   j.kval[0] = h->tiling.k;
   if (use_generic(h)) return RK4_EUNSUPPORTED;
   j.Gval[0] = W - 8 * h->tiling.k;
-  j.ntiles[0] = tiles_for(h, j.Gval[0]);
+  if (h->nchains > 1) {
+    j.bt[0] = dev_ktables(h, w, L, 0);
+    j.ntiles[0] = j.bt[0].nfull + j.bt[0].npacked;
+  } else {
+    j.ntiles[0] = tiles_for(h, j.Gval[0]);
+  }
   j.nmain = 1;
   j.ntail = 0;
   j.hdr = reinterpret_cast<WsHeader *>(w + L.hdr);

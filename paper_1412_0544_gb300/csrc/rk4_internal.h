@@ -46,6 +46,31 @@ struct WsHeader {
   unsigned char pad[224];
 };
 
+// A piece of one batch chain placed in a shared ("packed") tile: the chain's last partial piece
+// of interior sites (or the whole chain when it is shorter than a tile's interior), with its own
+// halo of H sites on each side.  Several segments lie side by side in one tile; each thread's
+// sites belong to one segment because o and L are multiples of the sites per thread.
+struct SegDesc {
+  int64_t g0;     // first interior site (chain-local index)
+  int32_t chain;  // index into the chain table
+  int32_t o;      // first tile slot of the segment's window
+  int32_t cnt;    // interior sites
+  int32_t L;      // window length in slots: H + cnt + H rounded up to a multiple of the sites per thread
+};
+
+// The tiles of one launch over a batch: first the full tiles (G interior sites each) of every
+// chain, numbered chain by chain (full_prefix: first full tile of each chain, nchains + 1
+// entries), then the packed tiles (pack_prefix: first segment of each packed tile, npacked + 1
+// entries, into segs).  A chain of n sites has floor(n / G) full tiles and, when G does not
+// divide n, one segment.
+struct BatchTiles {
+  const int32_t *full_prefix;
+  const int32_t *pack_prefix;
+  const SegDesc *segs;
+  int64_t nfull;
+  int64_t npacked;
+};
+
 // Arguments of one blocked launch (one chain, or a batch through a chain table).
 struct BlockedJob {
   const void *in;    // state read by this launch
@@ -55,7 +80,9 @@ struct BlockedJob {
   int nchains;       // 1: use `one`; >1: use `chains` / `tile_prefix`
   ChainDesc one;
   const ChainDesc *chains;      // device table (batches)
-  const int32_t *tile_prefix;   // device, nchains + 1 entries: first tile of each chain
+  const int32_t *tile_prefix;   // device, nchains + 1 entries: first tile of each chain (unpacked batches)
+  BatchTiles bt;                // packed batches: full and packed tiles (used when `packed`)
+  int packed;                   // 1: the batch's tiles follow `bt`, 0: `tile_prefix`
   int K;                        // steps in this launch
   int G;                        // interior sites per tile
   int64_t ntiles;               // tiles in the launch
@@ -98,7 +125,7 @@ struct PersistentJob {
   int nchains;
   ChainDesc one;
   const ChainDesc *chains;
-  const int32_t *tile_prefix;   // nk arrays of (nchains + 1) entries: first tile of each chain
+  BatchTiles bt[4];             // batches: the tiles of a time block for each k (full, then packed)
   int nk;                       // distinct k values (1..4)
   int kval[4];                  // steps per time block
   int Gval[4];                  // interior sites per tile for each k

@@ -236,7 +236,8 @@ __device__ __forceinline__ void tile_load(R *tile, const R *__restrict__ src, in
   if (t0 >= 0 && t0 + W <= n) {
     if (!bounds_ok(hdr, in_range(off + t0, W, sites))) return;
     const R *s = src + (off + t0) * D;
-    if ((reinterpret_cast<uintptr_t>(s) & 15u) == 0 && ((total * (int)sizeof(R)) & 15) == 0) {
+    if ((reinterpret_cast<uintptr_t>(s) & 15u) == 0 && (reinterpret_cast<uintptr_t>(tile) & 15u) == 0 &&
+        ((total * (int)sizeof(R)) & 15) == 0) {
       const int nv = total * (int)sizeof(R) / 16;
       const int4 *s4 = reinterpret_cast<const int4 *>(s);
       int4 *t4 = reinterpret_cast<int4 *>(tile);
@@ -371,6 +372,103 @@ __device__ __forceinline__ void tile_item(const R *__restrict__ in, R *__restric
   __syncthreads();  // shared memory is reused by the next item
 }
 
+// Process one packed tile: segments s0 .. s1 - 1 of `segs`, side by side in slot order, each a
+// window [g0 - H, g0 + cnt + H + pad) of its own chain (wrapped or zero outside the chain like a
+// plain tile).  The neighbour exchange runs across segment borders as if the tile were one
+// chain: a wrong neighbour at a border, like a missing one at a tile end, spoils one more site
+// per stage, so after K steps only each segment's H-site halos are spoilt and its cnt interior
+// sites are exact.  Every thread's sites lie in one segment (o and L are multiples of V), so a
+// thread takes its chain's coupling strength and, for fixed ends, its ghost mask; threads past
+// the last segment advance zeros that are never stored.
+template <typename R, int MODEL, int V, bool KAHAN, bool COH>
+__device__ __forceinline__ void packed_tile_item(const R *__restrict__ in, R *__restrict__ out,
+                                                 const R *__restrict__ cin, R *__restrict__ cout,
+                                                 const ChainDesc *chains, const SegDesc *segs, int s0, int s1,
+                                                 int K, const Coef<R> &cf, unsigned char *smem, int64_t sites,
+                                                 WsHeader *hdr) {
+  constexpr int D = Dim<MODEL>::D;
+  R *edge = reinterpret_cast<R *>(smem);
+  R *tl = edge + edge_values(V);
+  const int W = blockDim.x * V;
+  R *ctl = tl + W * D;
+  const int H = 4 * K;
+
+  int used = 0;  // slots covered by the segments (they are in slot order)
+  for (int s = s0; s < s1; ++s) {
+    const SegDesc sd = segs[s];
+    if (!bounds_ok(hdr, sd.o >= used && sd.L >= 0 && sd.o + sd.L <= W)) continue;
+    const ChainDesc ch = chains[sd.chain];
+    tile_load<R, D, COH>(tl + sd.o * D, in, ch.off, ch.n, ch.bc, sd.g0 - H, sd.L, sites, hdr);
+    if constexpr (KAHAN) tile_load<R, D, COH>(ctl + sd.o * D, cin, ch.off, ch.n, ch.bc, sd.g0 - H, sd.L, sites, hdr);
+    used = sd.o + sd.L;
+  }
+  for (int e = used * D + threadIdx.x; e < W * D; e += blockDim.x) {
+    tl[e] = R(0);
+    if constexpr (KAHAN) ctl[e] = R(0);
+  }
+  __syncthreads();
+
+  // this thread's segment: the last one starting at or before its first slot
+  const int base = threadIdx.x * V;
+  int my = -1;
+  if (s1 > s0) {
+    int lo = s0, hi = s1 - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (segs[mid].o <= base) lo = mid; else hi = mid - 1;
+    }
+    if (segs[lo].o <= base && base < segs[lo].o + segs[lo].L) my = lo;
+  }
+  Coef<R> c = cf;
+  uint32_t ghost = 0;
+  int rel = 0, cnt = 0;  // first site's position in the segment's window; the segment's interior sites
+  if (my >= 0) {
+    const SegDesc sd = segs[my];
+    const ChainDesc ch = chains[sd.chain];
+    c.kappa = (R)ch.kappa;
+    rel = base - sd.o;
+    cnt = sd.cnt;
+    if (ch.bc == FIXED) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int64_t g = sd.g0 - H + rel + v;
+        if (g < 0 || g >= ch.n) ghost |= 1u << v;
+      }
+    }
+  }
+
+  R y[V][D], cmp[V][D];
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      y[v][d] = tl[(base + v) * D + d];
+      if constexpr (KAHAN) cmp[v][d] = ctl[(base + v) * D + d]; else cmp[v][d] = R(0);
+    }
+  tile_advance<R, MODEL, V, KAHAN, true>(y, cmp, ghost, K, c, edge);
+
+  bool bad = false;  // a stored (interior) value is NaN or infinite
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const bool stored = my >= 0 && rel + v >= H && rel + v < H + cnt;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      tl[(base + v) * D + d] = y[v][d];
+      if constexpr (KAHAN) ctl[(base + v) * D + d] = cmp[v][d];
+      bad |= stored && nonfinite(y[v][d]);
+    }
+  }
+  report_nonfinite(hdr, __syncthreads_or(bad));
+  for (int s = s0; s < s1; ++s) {
+    const SegDesc sd = segs[s];
+    if (sd.cnt <= 0 || !bounds_ok(hdr, sd.o >= 0 && sd.o + sd.L <= W && sd.cnt + 2 * H <= sd.L)) continue;
+    const ChainDesc ch = chains[sd.chain];
+    tile_store<R, D>(out, tl, ch.off, sd.o + H, sd.g0, sd.cnt, sites, W, hdr);
+    if constexpr (KAHAN) tile_store<R, D>(cout, ctl, ch.off, sd.o + H, sd.g0, sd.cnt, sites, W, hdr);
+  }
+  __syncthreads();  // shared memory is reused by the next item
+}
+
 // Locate the chain of a tile index through the prefix array (first tile of each chain).
 __device__ __forceinline__ int find_chain(const int32_t *prefix, int nchains, int64_t tile) {
   int lo = 0, hi = nchains - 1;
@@ -379,6 +477,25 @@ __device__ __forceinline__ int find_chain(const int32_t *prefix, int nchains, in
     if (prefix[mid] <= tile) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+
+// Item `item` of a batch launch laid out by bt: a full tile of one chain, or a packed tile.
+template <typename R, int MODEL, int V, bool KAHAN, bool COH>
+__device__ __forceinline__ void batch_item(const R *__restrict__ in, R *__restrict__ out, const R *__restrict__ cin,
+                                           R *__restrict__ cout, const ChainDesc *chains, int nchains,
+                                           const BatchTiles &bt, int64_t item, int K, int G, const Coef<R> &cf,
+                                           unsigned char *smem, int64_t sites, WsHeader *hdr) {
+  if (item < bt.nfull) {
+    const int ci = find_chain(bt.full_prefix, nchains, item);
+    const ChainDesc ch = chains[ci];
+    Coef<R> c = cf;
+    c.kappa = (R)ch.kappa;
+    tile_item<R, MODEL, V, KAHAN, COH>(in, out, cin, cout, ch, item - bt.full_prefix[ci], K, G, c, smem, sites, hdr);
+  } else {
+    const int64_t p = item - bt.nfull;
+    packed_tile_item<R, MODEL, V, KAHAN, COH>(in, out, cin, cout, chains, bt.segs, bt.pack_prefix[p],
+                                              bt.pack_prefix[p + 1], K, cf, smem, sites, hdr);
+  }
 }
 
 template <typename R> __host__ __device__ inline Coef<R> to_coef(const CoefD &c, double kappa) {

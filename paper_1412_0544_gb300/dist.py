@@ -121,18 +121,39 @@ def exchange_ghosts(ext, part: dict, ghost: int, left, right):
         ext[sl].copy_(buf)
 
 
-def integrate_decomposed(ext, comp, part: dict, ghost: int, reach: int, nsteps: int, integrate, left, right):
+def exchange_ghosts_host(ext, part: dict, ghost: int, left, right):
+    """exchange_ghosts for a block held in device memory when the process group's backend moves
+    host tensors (gloo): only the block's edges travel through host memory -- its two ghost
+    zones and the `ghost` sites next to each -- and the received ghost zones are copied back."""
+    import torch
+    gl, n, gr = part["ghost_left"], part["sites"], part["ghost_right"]
+    if n >= 2 * ghost:
+        small = torch.cat([ext[:gl + ghost].cpu(), ext[gl + n - ghost:].cpu()])
+        small_part = {"ghost_left": gl, "sites": 2 * ghost, "ghost_right": gr}
+    else:
+        small = ext.cpu()
+        small_part = part
+    exchange_ghosts(small, small_part, ghost, left, right)
+    if gl:
+        ext[:gl].copy_(small[:gl])
+    if gr:
+        ext[gl + n:].copy_(small[small.shape[0] - gr:])
+
+
+def integrate_decomposed(ext, comp, part: dict, ghost: int, reach: int, nsteps: int, integrate, left, right,
+                         exchange=exchange_ghosts):
     """Advance this rank's part nsteps steps: swap ghost zones, run `integrate(ext, comp, m)` for
     m = min(floor(ghost / reach), steps left) steps on the part as a fixed-end chain, repeat.
-    On a GPU `integrate` is rk4_chain_integrate on a fixed-end handle of the block's length."""
+    On a GPU `integrate` is rk4_chain_integrate on a fixed-end handle of the block's length, and
+    `exchange` is exchange_ghosts (a device-capable backend) or exchange_ghosts_host (gloo)."""
     period = ghost // reach if (left is not None or right is not None) else max(nsteps, 1)
     if period < 1:
         raise ValueError("ghost zones narrower than one step's reach")
     done = 0
     while done < nsteps:
         m = min(period, nsteps - done)
-        exchange_ghosts(ext, part, ghost, left, right)
+        exchange(ext, part, ghost, left, right)
         if comp is not None:
-            exchange_ghosts(comp, part, ghost, left, right)
+            exchange(comp, part, ghost, left, right)
         integrate(ext, comp, m)
         done += m

@@ -111,6 +111,11 @@ def cases():
                                                                            tiling=(128, 4, 4), nsteps=9)
         c[f"batch_blocked_p{prec}"] = lambda rk, torch, p=prec: _batch(rk, torch, prec=p, kernel=2,
                                                                         tiling=(256, 4, 2), nsteps=9)
+        # packed batch tiles with one, two and eight sites per thread (segment windows start
+        # at multiples of v slots, so shared-memory tile offsets of every alignment occur)
+        for t, kern in (((256, 1, 2), 2), ((128, 2, 3), 3), ((128, 8, 4), 2)):
+            c[f"batch_packed_{kern}_{t}_p{prec}"] = lambda rk, torch, p=prec, t=t, kern=kern: _batch(
+                rk, torch, prec=p, kernel=kern, tiling=t, nsteps=2 * t[2] + 1)
         c[f"batch_staged_p{prec}"] = lambda rk, torch, p=prec: _batch(rk, torch, prec=p, kernel=1,
                                                                        tiling=(256, 4, 2), nsteps=3)
         c[f"domain_p{prec}"] = lambda rk, torch, p=prec: _domain(rk, torch, prec=p, nsteps=13)

@@ -165,7 +165,8 @@ ext[part["ghost_left"]:part["ghost_left"] + part["sites"]] = torch.from_numpy(
 def integrate(e, c, m):
     e.copy_(torch.from_numpy(oracle.rk4_integrate(e.numpy(), model, 1, 0.01, m)))
 left, right = d.neighbours(rank, world, bc == 0)
-d.integrate_decomposed(ext, None, part, ghost, 4, nsteps, integrate, left, right)
+exchange = d.exchange_ghosts_host if sys.argv[4] == "host" else d.exchange_ghosts
+d.integrate_decomposed(ext, None, part, ghost, 4, nsteps, integrate, left, right, exchange=exchange)
 mine = ext[part["ghost_left"]:part["ghost_left"] + part["sites"]].contiguous()
 chunks = [torch.zeros_like(mine) for _ in range(world)]  # n splits evenly over the ranks
 dist.all_gather(chunks, mine)
@@ -176,14 +177,16 @@ dist.destroy_process_group()
 """
 
 
-@pytest.mark.parametrize("bc,model,port", [(PER, 0, 29541), (FIX, 1, 29542)])
-def test_decomposition_two_gloo_ranks(tmp_path, bc, model, port):
-    """One part per CPU rank, ghost zones swapped by point-to-point messages, parts integrated
-    by the oracle: the gathered chain equals the undivided oracle run bit for bit."""
+@pytest.mark.parametrize("bc,model,port,exchange", [(PER, 0, 29541, "direct"), (FIX, 1, 29542, "direct"),
+                                                     (PER, 1, 29543, "host"), (FIX, 0, 29544, "host")])
+def test_decomposition_two_gloo_ranks(tmp_path, bc, model, port, exchange):
+    """One part per CPU rank, ghost zones swapped by point-to-point messages (directly, or
+    through the edge-only host staging that device blocks use), parts integrated by the oracle:
+    the gathered chain equals the undivided oracle run bit for bit."""
     script = tmp_path / "w.py"
     script.write_text(_GLOO_DOMAIN)
     env = dict(os.environ, MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE="2")
-    procs = [subprocess.Popen([sys.executable, str(script), ROOT, str(bc), str(model)],
+    procs = [subprocess.Popen([sys.executable, str(script), ROOT, str(bc), str(model), exchange],
                               env=dict(env, RANK=str(r), LOCAL_RANK=str(r)), stdout=subprocess.PIPE,
                               stderr=subprocess.PIPE, text=True) for r in range(2)]
     outs = []

@@ -12,6 +12,11 @@ where e = |a - b| / |b| (2-norms) and l_min, l_max are the extreme eigenvalues o
 omega0^2 + 4 kappa for the harmonic chain (the p block is the identity; the q block is
 omega0^2 + kappa times a graph Laplacian with spectrum in [0, 4]).  The test measures e against
 the FP64 oracle and asserts the FP32 energy drift within that bound of RK4's exact drift.
+
+Beyond that bound, the FP32-Kahan drift is pinned to a stated multiple of RK4's own drift: the
+FP32 rounding adds about 22 times RK4's exact modal drift (+1.74e-8 against -8.35e-10 after
+1000 steps of dt = 0.01, measured at N = 2^16 with both boundaries and at N = 2^24 alike, so it
+is systematic rather than a random walk that would shrink with N); the test allows 50 times.
 """
 import numpy as np
 import pytest
@@ -26,6 +31,7 @@ pytestmark = pytest.mark.gpu
 PER, FIX = 0, 1
 HAR = 1
 KAPPA, OMEGA0, DT, T = 1.0, 1.0, 0.01, 1000
+FP32_DRIFT_MULTIPLE = 50.0  # allowed |FP32 drift - RK4 drift| in units of |RK4 drift| (measured 22)
 
 
 @pytest.fixture(scope="module")
@@ -86,3 +92,4 @@ def test_fp32_kahan_energy_drift_bounded_by_state_error(rk, bc):
     assert abs(e0 - e0_modal) <= 1e-12 * e0_modal  # the start values are exact in both precisions
     assert e2 <= FP32_KAHAN_TOL
     assert abs(drift - pred) <= bound
+    assert abs(drift - pred) <= FP32_DRIFT_MULTIPLE * abs(pred)
