@@ -23,14 +23,6 @@ __global__ void __launch_bounds__(BlockedBounds<MODEL, V, KAHAN, HET>::threads,
     k_blocked(BlockedJob job, Coef<R> cf) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t item = blockIdx.x;
-  if constexpr (!HET) {
-    if (job.nchains > 1 && job.packed) {
-      batch_item<R, MODEL, V, KAHAN, false>(static_cast<const R *>(job.in), static_cast<R *>(job.out),
-                                            static_cast<const R *>(job.cin), static_cast<R *>(job.cout), job.chains,
-                                            job.nchains, job.bt, item, job.K, job.G, cf, smem, job.total, job.hdr);
-      return;
-    }
-  }
   ChainDesc ch;
   int64_t tile = item;
   Coef<R> c = cf;
@@ -48,6 +40,21 @@ __global__ void __launch_bounds__(BlockedBounds<MODEL, V, KAHAN, HET>::threads,
                                             static_cast<const R *>(job.sp));
 }
 
+// The packed tiles of a batch launch (one block per packed tile; the full tiles go to
+// k_blocked).  A kernel of its own, so that the segment bookkeeping does not weigh on the
+// register budget of k_blocked, which runs nearly every tile.
+template <typename R, int MODEL, int V, bool KAHAN>
+__global__ void __launch_bounds__(BlockedBounds<MODEL, V, KAHAN, false>::threads,
+                                  BlockedBounds<MODEL, V, KAHAN, false>::min_blocks)
+    k_blocked_packed(BlockedJob job, Coef<R> cf) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int64_t p = blockIdx.x;
+  packed_tile_item<R, MODEL, V, KAHAN, false>(static_cast<const R *>(job.in), static_cast<R *>(job.out),
+                                              static_cast<const R *>(job.cin), static_cast<R *>(job.cout), job.chains,
+                                              job.bt.segs, job.bt.pack_prefix[p], job.bt.pack_prefix[p + 1], job.K, cf,
+                                              smem, job.total, job.hdr);
+}
+
 size_t blocked_smem_bytes(int model, bool fp32, int v, int block, bool het) {
   const int D = model == ROESSLER ? 3 : 2;
   const int P = model == ROESSLER ? 4 : 2;
@@ -62,8 +69,15 @@ static cudaError_t launch_one(int block, const BlockedJob &job, const CoefD &cfd
   if (attr_err != cudaSuccess) return attr_err;
   const size_t smem = blocked_smem_bytes(MODEL, KAHAN, V, block, HET);
   Coef<R> cf = to_coef<R>(cfd, cfd.kappa);
-  if (job.ntiles <= 0) return cudaSuccess;
-  k_blocked<R, MODEL, V, KAHAN, HET><<<(unsigned)job.ntiles, block, smem, st>>>(job, cf);
+  if (job.ntiles > 0) k_blocked<R, MODEL, V, KAHAN, HET><<<(unsigned)job.ntiles, block, smem, st>>>(job, cf);
+  if constexpr (!HET) {
+    if (job.nchains > 1 && job.packed && job.bt.npacked > 0) {
+      static PerDevice attr_p;
+      const cudaError_t e = set_smem_limit_once(k_blocked_packed<R, MODEL, V, KAHAN>, 200 * 1024, attr_p);
+      if (e != cudaSuccess) return e;
+      k_blocked_packed<R, MODEL, V, KAHAN><<<(unsigned)job.bt.npacked, block, smem, st>>>(job, cf);
+    }
+  }
   return cudaGetLastError();
 }
 

@@ -131,7 +131,7 @@ __device__ __forceinline__ void gen_tile_advance(R (&y)[V][Dim<MODEL>::D], R (&c
                                                  const Tableau<R> &tb, R *edge) {
   constexpr int D = Dim<MODEL>::D;
   static_assert(V >= 2, "the generic kernel holds at least two sites per thread");
-  constexpr int NT = gen_max_threads(V);
+  constexpr int NT = kGenEdgeThreads;
   using R2 = typename Pair<R>::T;
   const int tid = threadIdx.x;
   const int lt = tid > 0 ? tid - 1 : tid;                           // left neighbour thread
@@ -147,14 +147,14 @@ __device__ __forceinline__ void gen_tile_advance(R (&y)[V][Dim<MODEL>::D], R (&c
       if (!gen_stage_needed<SHAPE>(j)) continue;  // a compiled shape's dead stage: nothing reads it
       R u[V][D];
       R ext[V + 4];  // ext[2 + v] = x of site v; two neighbours on each side
+      R2 *head = reinterpret_cast<R2 *>(edge) + parity * 2 * NT;  // (first, second) per thread
+      R2 *tail = head + NT;                                         // (second-last, last) per thread
+      parity ^= 1;
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         gen_stage_state<R, D, SHAPE>(j, tb, y[v], k[v], u[v]);
         ext[2 + v] = (MASK && ((ghost >> v) & 1u)) ? R(0) : u[v][0];
       }
-      R2 *head = reinterpret_cast<R2 *>(edge) + parity * 2 * NT;  // (first, second) per thread
-      R2 *tail = head + NT;                                         // (second-last, last) per thread
-      parity ^= 1;
       R2 hv, tv;
       hv.x = ext[2];
       hv.y = ext[3];
@@ -185,121 +185,121 @@ __device__ __forceinline__ void gen_tile_advance(R (&y)[V][Dim<MODEL>::D], R (&c
   }
 }
 
+// The generic tile kernel.  With a compiled tableau shape (STREAM) it runs as a streaming
+// loop: a resident set of blocks (grid sized by the host to what fits on the GPU) walks the
+// tiles, block b taking tiles b, b + gridDim.x, ...  While a block computes one tile, the next
+// one's window is already on its way into the second of two shared-memory buffers (cp.async),
+// so a tile's load latency is hidden behind the previous tile's arithmetic.  That lets short
+// launches (small k, and so a small halo of redundant sites) run without exposed load time,
+// which matters here: the generic scheme's halo is s' x range sites per side and step (12 for
+// Dormand-Prince 5 with second neighbours).  The run-time-shape form (SHAPE = 0) processes one
+// tile per block (a loop around it would keep the tableau's coefficients in registers).
+// Shared memory: edge[gen_edge_values(V)] | buffer 0: tile[W*D] (+ ctile[W*D]) | buffer 1
+// (streaming only).
 template <typename R, int MODEL, int V, int RANGE, bool KAHAN, uint64_t SHAPE = 0>
-__global__ void __launch_bounds__(gen_max_threads(V)) k_gen_blocked(BlockedJob job, Coef<R> cf, R kappa2,
-                                                                     Tableau<R> tb, int H) {
+__global__ void __launch_bounds__(GenBounds<R, V, SHAPE>::threads) k_gen_blocked(BlockedJob job, Coef<R> cf,
+                                                                                 R kappa2, Tableau<R> tb, int H) {
   constexpr int D = Dim<MODEL>::D;
+  constexpr bool STREAM = SHAPE != 0;
   extern __shared__ __align__(16) unsigned char smem[];
   R *edge = reinterpret_cast<R *>(smem);
-  R *tl = edge + gen_edge_values(V);
   const int W = blockDim.x * V;
-  R *ctl = tl + W * D;
-  const int64_t item = blockIdx.x;
-  ChainDesc ch;
-  int64_t tile = item;
-  Coef<R> c = cf;
-  if (job.nchains == 1) {
-    ch = job.one;
-  } else {
-    const int ci = find_chain(job.tile_prefix, job.nchains, item);
-    ch = job.chains[ci];
-    tile = item - job.tile_prefix[ci];
-    c.kappa = (R)ch.kappa;
-  }
   const int G = job.G;
-  const int64_t t0 = tile * (int64_t)G - H;
-  tile_load<R, D, false>(tl, static_cast<const R *>(job.in), ch.off, ch.n, ch.bc, t0, W, job.total, job.hdr);
-  if constexpr (KAHAN)
-    tile_load<R, D, false>(ctl, static_cast<const R *>(job.cin), ch.off, ch.n, ch.bc, t0, W, job.total, job.hdr);
-  __syncthreads();
-  R y[V][D], cmp[V][D];
-  const int base = threadIdx.x * V;
-#pragma unroll
-  for (int v = 0; v < V; ++v)
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      y[v][d] = tl[(base + v) * D + d];
-      if constexpr (KAHAN) cmp[v][d] = ctl[(base + v) * D + d]; else cmp[v][d] = R(0);
+  const int tsize = W * D * (KAHAN ? 2 : 1);  // one buffer: tile and compensation tile
+  R *const buf0 = edge + gen_edge_values(V);
+  const R *in = static_cast<const R *>(job.in);
+  const R *cin = static_cast<const R *>(job.cin);
+
+  // chain, chain-local tile index and coupling of item `it`
+  auto locate = [&](int64_t it, ChainDesc &ch, int64_t &tile, Coef<R> &c) {
+    c = cf;
+    if (job.nchains == 1) {
+      ch = job.one;
+      tile = it;
+    } else {
+      const int ci = find_chain(job.tile_prefix, job.nchains, it);
+      ch = job.chains[ci];
+      tile = it - job.tile_prefix[ci];
+      c.kappa = (R)ch.kappa;
     }
-  const bool edge_tile = (ch.bc == FIXED) && (t0 < 0 || t0 + W > ch.n);
-  if (edge_tile) {
-    uint32_t ghost = 0;
+  };
+  auto issue = [&](int64_t it, R *buf) {
+    ChainDesc ch;
+    int64_t tile;
+    Coef<R> c;
+    locate(it, ch, tile, c);
+    const int64_t t0 = tile * (int64_t)G - H;
+    tile_load_async<R, D>(buf, in, ch.off, ch.n, ch.bc, t0, W, job.total, job.hdr);
+    if constexpr (KAHAN) tile_load_async<R, D>(buf + W * D, cin, ch.off, ch.n, ch.bc, t0, W, job.total, job.hdr);
+    cp_async_commit();
+  };
+
+  int64_t item = blockIdx.x;
+  if (item >= job.ntiles) return;
+  issue(item, buf0);
+  int cur = 0;
+  for (;;) {
+    const int64_t next = item + gridDim.x;
+    if (STREAM && next < job.ntiles) {
+      issue(next, buf0 + (cur ^ 1) * tsize);  // that buffer was released by the last iteration's barrier
+      cp_async_wait<1>();                     // this tile's copies are complete, the next one's may run on
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    R *tl = buf0 + cur * tsize;
+    R *ctl = tl + W * D;
+    ChainDesc ch;
+    int64_t tile;
+    Coef<R> c;
+    locate(item, ch, tile, c);
+    const int64_t t0 = tile * (int64_t)G - H;
+    R y[V][D], cmp[V][D];
+    const int base = threadIdx.x * V;
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        y[v][d] = tl[(base + v) * D + d];
+        if constexpr (KAHAN) cmp[v][d] = ctl[(base + v) * D + d]; else cmp[v][d] = R(0);
+      }
+    const bool edge_tile = (ch.bc == FIXED) && (t0 < 0 || t0 + W > ch.n);
+    if (edge_tile) {
+      uint32_t ghost = 0;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int64_t g = t0 + base + v;
+        if (g < 0 || g >= ch.n) ghost |= 1u << v;
+      }
+      gen_tile_advance<R, MODEL, V, RANGE, KAHAN, true, SHAPE>(y, cmp, ghost, job.K, c, kappa2, tb, edge);
+    } else {
+      gen_tile_advance<R, MODEL, V, RANGE, KAHAN, false, SHAPE>(y, cmp, 0u, job.K, c, kappa2, tb, edge);
+    }
+    const int64_t g0 = t0 + H;
+    const int64_t rem = ch.n - g0;
+    const int cnt = (int)(rem < G ? rem : G);
+    bool bad = false;  // a stored (interior) value is NaN or infinite
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      const int64_t g = t0 + base + v;
-      if (g < 0 || g >= ch.n) ghost |= 1u << v;
-    }
-    gen_tile_advance<R, MODEL, V, RANGE, KAHAN, true, SHAPE>(y, cmp, ghost, job.K, c, kappa2, tb, edge);
-  } else {
-    gen_tile_advance<R, MODEL, V, RANGE, KAHAN, false, SHAPE>(y, cmp, 0u, job.K, c, kappa2, tb, edge);
-  }
-  const int64_t g0 = t0 + H;
-  const int64_t rem = ch.n - g0;
-  const int cnt = (int)(rem < G ? rem : G);
-  bool bad = false;  // a stored (interior) value is NaN or infinite
+      const bool stored = base + v >= H && base + v < H + cnt;
 #pragma unroll
-  for (int v = 0; v < V; ++v) {
-    const bool stored = base + v >= H && base + v < H + cnt;
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      tl[(base + v) * D + d] = y[v][d];
-      if constexpr (KAHAN) ctl[(base + v) * D + d] = cmp[v][d];
-      bad |= stored && nonfinite(y[v][d]);
+      for (int d = 0; d < D; ++d) {
+        tl[(base + v) * D + d] = y[v][d];
+        if constexpr (KAHAN) ctl[(base + v) * D + d] = cmp[v][d];
+        bad |= stored && nonfinite(y[v][d]);
+      }
     }
-  }
-  report_nonfinite(job.hdr, __syncthreads_or(bad));
-  if (cnt > 0) {
-    tile_store<R, D>(static_cast<R *>(job.out), tl, ch.off, H, g0, cnt, job.total, W, job.hdr);
-    if constexpr (KAHAN) tile_store<R, D>(static_cast<R *>(job.cout), ctl, ch.off, H, g0, cnt, job.total, W, job.hdr);
-  }
-}
-
-template <typename R, int MODEL, int V, int RANGE, bool KAHAN>
-static int gen_max_threads_one() {
-  cudaFuncAttributes a;
-  if (cudaFuncGetAttributes(&a, k_gen_blocked<R, MODEL, V, RANGE, KAHAN>) != cudaSuccess) return 0;
-  return a.maxThreadsPerBlock;
-}
-
-template <int MODEL, int RANGE>
-static int gen_max_threads_m(bool fp32, int v) {
-  if (v == 2) return fp32 ? gen_max_threads_one<float, MODEL, 2, RANGE, true>() : gen_max_threads_one<double, MODEL, 2, RANGE, false>();
-  if (v == 4) return fp32 ? gen_max_threads_one<float, MODEL, 4, RANGE, true>() : gen_max_threads_one<double, MODEL, 4, RANGE, false>();
-  return 0;
-}
-
-int gen_blocked_max_threads(int model, bool fp32, int range, int v) {
-  if (model == ROESSLER) return range == 1 ? gen_max_threads_m<ROESSLER, 1>(fp32, v) : gen_max_threads_m<ROESSLER, 2>(fp32, v);
-  return range == 1 ? gen_max_threads_m<HARMONIC, 1>(fp32, v) : gen_max_threads_m<HARMONIC, 2>(fp32, v);
-}
-
-size_t gen_blocked_smem_bytes(int model, bool fp32, int v, int block) {
-  const int D = model == ROESSLER ? 3 : 2;
-  const size_t rs = fp32 ? 4 : 8;
-  return (size_t)gen_edge_values(v) * rs + (size_t)block * v * D * rs * (fp32 ? 2 : 1);
-}
-
-// ---- launchers ------------------------------------------------------------------------------
-
-template <typename R>
-static Tableau<R> to_tableau(const TableauD &t, double dt) {
-  Tableau<R> r{};
-  r.s = t.s;
-  for (int j = 0; j < kMaxStages; ++j) {
-    r.anz[j] = 0;
-    for (int m = 0; m < kMaxStages; ++m) {
-      const double a = (j < t.s && m < j) ? t.a[j][m] : 0.0;
-      r.adt[j][m] = (R)(a * dt);
-      if (a != 0.0) r.anz[j] |= 1u << m;
+    report_nonfinite(job.hdr, __syncthreads_or(bad));
+    if (cnt > 0) {
+      tile_store<R, D>(static_cast<R *>(job.out), tl, ch.off, H, g0, cnt, job.total, W, job.hdr);
+      if constexpr (KAHAN) tile_store<R, D>(static_cast<R *>(job.cout), ctl, ch.off, H, g0, cnt, job.total, W, job.hdr);
     }
+    if constexpr (!STREAM) break;
+    __syncthreads();  // the buffer is refilled two iterations on; nobody may still read it
+    cur ^= 1;
+    item = next;
+    if (item >= job.ntiles) break;
   }
-  r.bnz = 0;
-  for (int m = 0; m < kMaxStages; ++m) {
-    const double b = m < t.s ? t.b[m] : 0.0;
-    r.bdt[m] = (R)(b * dt);
-    if (b != 0.0) r.bnz |= 1u << m;
-  }
-  return r;
 }
 
 // The nonzero pattern of a tableau (see shape_a_bit): the key of the compiled shapes.
@@ -324,6 +324,72 @@ constexpr uint64_t kShapeDopri5 =
     shape_a_bit(5, 0) | shape_a_bit(5, 1) | shape_a_bit(5, 2) | shape_a_bit(5, 3) | shape_a_bit(5, 4) |
     shape_a_bit(6, 0) | shape_a_bit(6, 2) | shape_a_bit(6, 3) | shape_a_bit(6, 4) | shape_a_bit(6, 5) |
     shape_b_bit(0) | shape_b_bit(2) | shape_b_bit(3) | shape_b_bit(4) | shape_b_bit(5);
+
+// The compiled shape a tableau runs with at v sites per thread (0: the run-time-shape kernel).
+static uint64_t compiled_shape(const TableauD &t, int v) {
+  if (v != 4) return 0;
+  const uint64_t sh = tableau_shape(t);
+  return (sh == kShapeDopri5 || sh == kShapeRK4) ? sh : 0;
+}
+
+template <typename R, int MODEL, int V, int RANGE, bool KAHAN, uint64_t SHAPE>
+static int gen_max_threads_s() {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, k_gen_blocked<R, MODEL, V, RANGE, KAHAN, SHAPE>) != cudaSuccess) return 0;
+  return a.maxThreadsPerBlock;
+}
+
+template <typename R, int MODEL, int V, int RANGE, bool KAHAN>
+static int gen_max_threads_one(uint64_t shape) {
+  if constexpr (V == 4) {
+    if (shape == kShapeDopri5) return gen_max_threads_s<R, MODEL, V, RANGE, KAHAN, kShapeDopri5>();
+    if (shape == kShapeRK4) return gen_max_threads_s<R, MODEL, V, RANGE, KAHAN, kShapeRK4>();
+  }
+  return gen_max_threads_s<R, MODEL, V, RANGE, KAHAN, 0>();
+}
+
+template <int MODEL, int RANGE>
+static int gen_max_threads_m(bool fp32, int v, uint64_t sh) {
+  if (v == 2) return fp32 ? gen_max_threads_one<float, MODEL, 2, RANGE, true>(sh) : gen_max_threads_one<double, MODEL, 2, RANGE, false>(sh);
+  if (v == 4) return fp32 ? gen_max_threads_one<float, MODEL, 4, RANGE, true>(sh) : gen_max_threads_one<double, MODEL, 4, RANGE, false>(sh);
+  return 0;
+}
+
+int gen_blocked_max_threads(int model, bool fp32, int range, int v, const TableauD &tb) {
+  const uint64_t sh = compiled_shape(tb, v);
+  if (model == ROESSLER) return range == 1 ? gen_max_threads_m<ROESSLER, 1>(fp32, v, sh) : gen_max_threads_m<ROESSLER, 2>(fp32, v, sh);
+  return range == 1 ? gen_max_threads_m<HARMONIC, 1>(fp32, v, sh) : gen_max_threads_m<HARMONIC, 2>(fp32, v, sh);
+}
+
+size_t gen_blocked_smem_bytes(int model, bool fp32, int v, int block, const TableauD &tb) {
+  const int D = model == ROESSLER ? 3 : 2;
+  const size_t rs = fp32 ? 4 : 8;
+  const size_t buffers = compiled_shape(tb, v) != 0 ? 2 : 1;  // the streaming form double-buffers
+  return (size_t)gen_edge_values(v) * rs + buffers * (size_t)block * v * D * rs * (fp32 ? 2 : 1);
+}
+
+// ---- launchers ------------------------------------------------------------------------------
+
+template <typename R>
+static Tableau<R> to_tableau(const TableauD &t, double dt) {
+  Tableau<R> r{};
+  r.s = t.s;
+  for (int j = 0; j < kMaxStages; ++j) {
+    r.anz[j] = 0;
+    for (int m = 0; m < kMaxStages; ++m) {
+      const double a = (j < t.s && m < j) ? t.a[j][m] : 0.0;
+      r.adt[j][m] = (R)(a * dt);
+      if (a != 0.0) r.anz[j] |= 1u << m;
+    }
+  }
+  r.bnz = 0;
+  for (int m = 0; m < kMaxStages; ++m) {
+    const double b = m < t.s ? t.b[m] : 0.0;
+    r.bdt[m] = (R)(b * dt);
+    if (b != 0.0) r.bnz |= 1u << m;
+  }
+  return r;
+}
 
 static int64_t staged_grid(int64_t total) {
   int64_t g = (total + 255) / 256;
@@ -369,8 +435,17 @@ static cudaError_t gen_blocked_s(int block, const BlockedJob &job, const CoefD &
   const cudaError_t attr_err = set_smem_limit_once(k_gen_blocked<R, MODEL, V, RANGE, KAHAN, SHAPE>, 200 * 1024, attr);
   if (attr_err != cudaSuccess) return attr_err;
   if (job.ntiles <= 0) return cudaSuccess;
-  const size_t smem = gen_blocked_smem_bytes(MODEL, KAHAN, V, block);
-  k_gen_blocked<R, MODEL, V, RANGE, KAHAN, SHAPE><<<(unsigned)job.ntiles, block, smem, st>>>(
+  const size_t smem = gen_blocked_smem_bytes(MODEL, KAHAN, V, block, td);
+  int64_t grid = job.ntiles;  // one tile per block, or
+  if constexpr (SHAPE != 0) {  // the streaming form: as many blocks as stay resident together
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, k_gen_blocked<R, MODEL, V, RANGE, KAHAN, SHAPE>, block, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    grid = std::min<int64_t>(job.ntiles, (int64_t)per_sm * sm_count());
+  }
+  k_gen_blocked<R, MODEL, V, RANGE, KAHAN, SHAPE><<<(unsigned)grid, block, smem, st>>>(
       job, to_coef<R>(cfd, cfd.kappa), (R)cfd.kappa2, to_tableau<R>(td, dt), H);
   return cudaGetLastError();
 }
@@ -379,7 +454,7 @@ template <typename R, int MODEL, int V, int RANGE, bool KAHAN>
 static cudaError_t gen_blocked_t(int block, const BlockedJob &job, const CoefD &cfd, const TableauD &td, double dt,
                                  int H, cudaStream_t st) {
   if constexpr (V == 4) {
-    const uint64_t sh = tableau_shape(td);
+    const uint64_t sh = compiled_shape(td, V);
     if (sh == kShapeDopri5) return gen_blocked_s<R, MODEL, V, RANGE, KAHAN, kShapeDopri5>(block, job, cfd, td, dt, H, st);
     if (sh == kShapeRK4) return gen_blocked_s<R, MODEL, V, RANGE, KAHAN, kShapeRK4>(block, job, cfd, td, dt, H, st);
   }

@@ -213,7 +213,7 @@ int tiling_valid(const rk4_chain *h, int block, int v, int k) {
     if (v != 2 && v != 4) return 0;
     const int H = halo(h, k);
     if (W - 2 * H < H) return 0;
-    if (gen_blocked_smem_bytes(h->model, h->fp32, v, block) > kMaxSmem) return 0;
+    if (gen_blocked_smem_bytes(h->model, h->fp32, v, block, h->tab) > kMaxSmem) return 0;
     return 1;
   }
   if (v != 1 && v != 2 && v != 4 && v != 8) return 0;
@@ -224,7 +224,7 @@ int tiling_valid(const rk4_chain *h, int block, int v, int k) {
 }
 
 int tiling_max_threads(const rk4_chain *h, int v) {
-  return use_generic(h) ? gen_blocked_max_threads(h->model, h->fp32, coupling_range(h), v)
+  return use_generic(h) ? gen_blocked_max_threads(h->model, h->fp32, coupling_range(h), v, h->tab)
                         : blocked_max_threads(h->model, h->fp32, v, use_het(h));
 }
 
@@ -505,9 +505,11 @@ cudaError_t enqueue_integrate(rk4_chain *h, int kernel, void *state, void *comp,
       j.K = k;
       j.G = W - 2 * halo(h, k);
       if (h->nchains > 1) {
+        // k_blocked takes the full tiles (or, unpacked, every tile); the packed tiles go to a
+        // second launch of their own kernel
         j.bt = dev_ktables(h, ws, L, ki);
         j.tile_prefix = j.bt.full_prefix;
-        j.ntiles = j.bt.nfull + j.bt.npacked;
+        j.ntiles = j.bt.nfull;
       } else {
         j.ntiles = tiles_for(h, j.G);
       }

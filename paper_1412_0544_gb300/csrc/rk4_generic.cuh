@@ -6,12 +6,16 @@
 
 namespace rk4d {
 
-// Largest block of the generic tile kernel by sites per thread (it keeps every stage slope
-// of every site in registers).
-__host__ __device__ constexpr int gen_max_threads(int v) { return v <= 4 ? 256 : 128; }
+// Largest block of the generic tile kernel (it keeps every stage slope of every site in
+// registers, so the register budget of a block decides): 512 threads for FP32 with two sites
+// per thread or a compiled tableau shape (at most 128 registers per thread), 256 otherwise.
+template <typename R, int V, uint64_t SHAPE> struct GenBounds {
+  static constexpr int threads = (sizeof(R) == 4 && (SHAPE != 0 || V == 2)) ? 512 : 256;
+};
 // Shared-memory values of the generic tile kernel's neighbour exchange: 2 parities x 2 pairs
-// of coupling coordinates per thread of the largest block.
-__host__ __device__ constexpr int gen_edge_values(int v) { return 2 * 4 * gen_max_threads(v); }
+// of coupling coordinates per thread of the largest block any instantiation allows.
+constexpr int kGenEdgeThreads = 512;
+__host__ __device__ constexpr int gen_edge_values(int v) { return (void)v, 2 * 4 * kGenEdgeThreads; }
 
 // The tableau in the working precision: a_jm dt and b_m dt rounded once on the host, plus
 // bit masks of the nonzero entries (zero entries are skipped, in every kernel alike).

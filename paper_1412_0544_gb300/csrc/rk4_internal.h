@@ -85,7 +85,7 @@ struct BlockedJob {
   int packed;                   // 1: the batch's tiles follow `bt`, 0: `tile_prefix`
   int K;                        // steps in this launch
   int G;                        // interior sites per tile
-  int64_t ntiles;               // tiles in the launch
+  int64_t ntiles;               // tiles of k_blocked in the launch (a packed batch's full tiles)
   const void *sp;               // per-site parameters of a heterogeneous chain, or NULL
   WsHeader *hdr;                // status word (non-finite results, debug bounds checks)
   int64_t total;                // sites in the state buffers
@@ -170,8 +170,8 @@ cudaError_t launch_gen_staged_step(int model, bool fp32, int range, const GenSta
                                    const TableauD &tb, double dt, cudaStream_t st);
 cudaError_t launch_gen_blocked(int model, bool fp32, int range, int v, int block, const BlockedJob &job,
                                const CoefD &cf, const TableauD &tb, double dt, int H, cudaStream_t st);
-size_t gen_blocked_smem_bytes(int model, bool fp32, int v, int block);
-int gen_blocked_max_threads(int model, bool fp32, int range, int v);
+size_t gen_blocked_smem_bytes(int model, bool fp32, int v, int block, const TableauD &tb);
+int gen_blocked_max_threads(int model, bool fp32, int range, int v, const TableauD &tb);
 size_t blocked_smem_bytes(int model, bool fp32, int v, int block, bool het = false);
 int blocked_max_threads(int model, bool fp32, int v, bool het = false);
 
