@@ -98,11 +98,16 @@ def code_only(src: str) -> str:
     return " ".join(src.split())
 
 
-def kernel_hash(read=None) -> str:
-    """Hash of the code (comments and spacing excluded) the FP64 blocked kernel is built from."""
+BLOCKED_SOURCES = ("rk4_device.cuh", "rk4_tile.cuh", "k_blocked.cu")
+GENERIC_SOURCES = ("rk4_device.cuh", "rk4_tile.cuh", "rk4_generic.cuh", "k_generic.cu")
+
+
+def kernel_hash(read=None, files=BLOCKED_SOURCES) -> str:
+    """Hash of the code (comments and spacing excluded) a kernel is built from: by default the
+    blocked kernel; GENERIC_SOURCES for the generic scheme's kernel."""
     read = read or (lambda f: open(os.path.join(ROOT, "paper_1412_0544_gb300", "csrc", f)).read())
     h = hashlib.sha256()
-    for f in ("rk4_device.cuh", "rk4_tile.cuh", "k_blocked.cu"):
+    for f in files:
         h.update(code_only(read(f)).encode())
     return h.hexdigest()[:16]
 
@@ -331,8 +336,9 @@ def periodic_fp64_extra(rk, torch, stream, n=N_SITES, nsteps=NSTEPS):
 
 
 def batch_extra(rk, torch, stream, precision, nsteps=NSTEPS):
-    """4096 chains, lengths log-uniform in [64, 65536], kappa ~ U[0.5, 2], mixed boundaries,
-    one persistent cooperative launch replayed from a CUDA graph."""
+    """4096 chains, lengths log-uniform in [64, 65536], kappa ~ U[0.5, 2], mixed boundaries:
+    the persistent cooperative launch (CUDA graph) and the autotuner's choice between it and
+    one blocked launch per k steps, beside one long chain at the same tiling."""
     import chain_inputs as ci
     lengths, kappa, bcs = ci.batch_spec(4096, seed=SEED)
     total = int(lengths.sum())
@@ -359,9 +365,28 @@ def batch_extra(rk, torch, stream, precision, nsteps=NSTEPS):
         out.update({"value": total * nsteps / el, "tiling": best,
                     "kernel": ("persistent cooperative" if kern == rk.RK4_KERNEL_PERSISTENT
                                else "blocked, one launch per k steps") + ", CUDA graph (autotuned)"})
-        return out
+        del st, cp, ws
     finally:
         rk.rk4_chain_destroy(h)
+    # one periodic chain of 2^24 sites with the same tiling and steps: the batch's rate against it
+    # measures what uneven chains cost (halos of every chain's last piece, packing, chain lookup)
+    n = N_SITES
+    h = rk.rk4_chain_create(rk.RK4_ROESSLER, precision, n, DT, rk.RK4_PERIODIC, None, stream)
+    try:
+        dt_ = torch.float32 if precision == rk.RK4_FP32_KAHAN else torch.float64
+        st = torch.empty((n, D), dtype=dt_, device="cuda")
+        rk.rk4_fill_uniform(st, n * D, SEED, 0, precision, stream)
+        cp = torch.zeros_like(st) if precision == rk.RK4_FP32_KAHAN else None
+        ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+        rk.rk4_chain_set_tiling(h, best["block"], best["v"], best["k"])
+        rk.rk4_chain_integrate(h, st, cp, ws, nsteps)
+        el = time_integrate(rk, h, st, cp, ws, nsteps, 1, torch)
+        out["single_chain_2e24_same_tiling"] = n * nsteps / el
+        out["ratio_to_single_chain"] = out["value"] / out["single_chain_2e24_same_tiling"]
+        del st, cp, ws
+    finally:
+        rk.rk4_chain_destroy(h)
+    return out
 
 
 def size_sweep(args):
@@ -524,6 +549,7 @@ def variant_extra(rk, torch, stream, precision, *, generic=False, het=False, n=N
         peak = FP32_INST_PEAK if fp32 else FP64_INST_PEAK
         return {"value": sps, "unit": "site-steps/s", "N": n, "steps": nsteps, "tiling": best,
                 "fp_inst_per_site_step": ops, "pipe_frac_of_measured": sps * ops / peak,
+                "kernel_hash": kernel_hash(files=GENERIC_SOURCES if generic else BLOCKED_SOURCES),
                 "scheme": ("Dormand-Prince 5 (7 stages) + second-neighbour coupling" if generic
                            else "heterogeneous chain, per-site a, b, c, kappa")}
     finally:

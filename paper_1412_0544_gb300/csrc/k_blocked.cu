@@ -17,12 +17,39 @@ template <int MODEL, int V, bool KAHAN, bool HET> struct BlockedBounds {
   static constexpr int min_blocks = kHetWide ? 3 : ((V >= 4 && KAHAN && !HET) ? 2 : 0);
 };
 
+// A batch launch's packed tiles (item p of them).  Not inlined: the segment bookkeeping then
+// takes registers only inside this call, and the tile loop of k_blocked, which runs nearly
+// every tile, keeps its own allocation (with the packed path inlined the FP32 tile kernel
+// spilled 120 bytes and ran 4 % slower; as a second kernel launched after each batch launch
+// its few blocks ran alone at the end of every launch).
+template <typename R, int MODEL, int V, bool KAHAN>
+__device__ __noinline__ void packed_tile_call(const void *in, void *out, const void *cin, void *cout,
+                                              const ChainDesc *chains, const SegDesc *segs, const int32_t *pack_prefix,
+                                              int64_t p, int K, Coef<R> cf, unsigned char *smem, int64_t sites,
+                                              WsHeader *hdr) {
+  packed_tile_item<R, MODEL, V, KAHAN, false>(static_cast<const R *>(in), static_cast<R *>(out),
+                                              static_cast<const R *>(cin), static_cast<R *>(cout), chains, segs,
+                                              pack_prefix[p], pack_prefix[p + 1], K, cf, smem, sites, hdr);
+}
+
 template <typename R, int MODEL, int V, bool KAHAN, bool HET>
 __global__ void __launch_bounds__(BlockedBounds<MODEL, V, KAHAN, HET>::threads,
                                   BlockedBounds<MODEL, V, KAHAN, HET>::min_blocks)
     k_blocked(BlockedJob job, Coef<R> cf) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int64_t item = blockIdx.x;
+  int64_t item = blockIdx.x;
+  if constexpr (!HET) {
+    if (job.nchains > 1 && job.packed) {
+      // a packed batch: its packed tiles come first, so that they run in the first wave beside
+      // full tiles instead of alone after the last one
+      if (item < job.bt.npacked) {
+        packed_tile_call<R, MODEL, V, KAHAN>(job.in, job.out, job.cin, job.cout, job.chains, job.bt.segs,
+                                             job.bt.pack_prefix, item, job.K, cf, smem, job.total, job.hdr);
+        return;
+      }
+      item -= job.bt.npacked;
+    }
+  }
   ChainDesc ch;
   int64_t tile = item;
   Coef<R> c = cf;
@@ -40,21 +67,6 @@ __global__ void __launch_bounds__(BlockedBounds<MODEL, V, KAHAN, HET>::threads,
                                             static_cast<const R *>(job.sp));
 }
 
-// The packed tiles of a batch launch (one block per packed tile; the full tiles go to
-// k_blocked).  A kernel of its own, so that the segment bookkeeping does not weigh on the
-// register budget of k_blocked, which runs nearly every tile.
-template <typename R, int MODEL, int V, bool KAHAN>
-__global__ void __launch_bounds__(BlockedBounds<MODEL, V, KAHAN, false>::threads,
-                                  BlockedBounds<MODEL, V, KAHAN, false>::min_blocks)
-    k_blocked_packed(BlockedJob job, Coef<R> cf) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int64_t p = blockIdx.x;
-  packed_tile_item<R, MODEL, V, KAHAN, false>(static_cast<const R *>(job.in), static_cast<R *>(job.out),
-                                              static_cast<const R *>(job.cin), static_cast<R *>(job.cout), job.chains,
-                                              job.bt.segs, job.bt.pack_prefix[p], job.bt.pack_prefix[p + 1], job.K, cf,
-                                              smem, job.total, job.hdr);
-}
-
 size_t blocked_smem_bytes(int model, bool fp32, int v, int block, bool het) {
   const int D = model == ROESSLER ? 3 : 2;
   const int P = model == ROESSLER ? 4 : 2;
@@ -69,15 +81,9 @@ static cudaError_t launch_one(int block, const BlockedJob &job, const CoefD &cfd
   if (attr_err != cudaSuccess) return attr_err;
   const size_t smem = blocked_smem_bytes(MODEL, KAHAN, V, block, HET);
   Coef<R> cf = to_coef<R>(cfd, cfd.kappa);
-  if (job.ntiles > 0) k_blocked<R, MODEL, V, KAHAN, HET><<<(unsigned)job.ntiles, block, smem, st>>>(job, cf);
-  if constexpr (!HET) {
-    if (job.nchains > 1 && job.packed && job.bt.npacked > 0) {
-      static PerDevice attr_p;
-      const cudaError_t e = set_smem_limit_once(k_blocked_packed<R, MODEL, V, KAHAN>, 200 * 1024, attr_p);
-      if (e != cudaSuccess) return e;
-      k_blocked_packed<R, MODEL, V, KAHAN><<<(unsigned)job.bt.npacked, block, smem, st>>>(job, cf);
-    }
-  }
+  // one block per full tile and (packed batches) one per packed tile
+  const int64_t grid = job.ntiles + ((!HET && job.nchains > 1 && job.packed) ? job.bt.npacked : 0);
+  if (grid > 0) k_blocked<R, MODEL, V, KAHAN, HET><<<(unsigned)grid, block, smem, st>>>(job, cf);
   return cudaGetLastError();
 }
 

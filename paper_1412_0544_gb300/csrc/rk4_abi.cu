@@ -505,8 +505,8 @@ cudaError_t enqueue_integrate(rk4_chain *h, int kernel, void *state, void *comp,
       j.K = k;
       j.G = W - 2 * halo(h, k);
       if (h->nchains > 1) {
-        // k_blocked takes the full tiles (or, unpacked, every tile); the packed tiles go to a
-        // second launch of their own kernel
+        // ntiles counts the full tiles (or, unpacked, every tile); the packed tiles follow them
+        // in the same launch
         j.bt = dev_ktables(h, ws, L, ki);
         j.tile_prefix = j.bt.full_prefix;
         j.ntiles = j.bt.nfull;

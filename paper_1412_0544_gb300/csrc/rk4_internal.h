@@ -58,11 +58,11 @@ struct SegDesc {
   int32_t L;      // window length in slots: H + cnt + H rounded up to a multiple of the sites per thread
 };
 
-// The tiles of one launch over a batch: first the full tiles (G interior sites each) of every
-// chain, numbered chain by chain (full_prefix: first full tile of each chain, nchains + 1
-// entries), then the packed tiles (pack_prefix: first segment of each packed tile, npacked + 1
-// entries, into segs).  A chain of n sites has floor(n / G) full tiles and, when G does not
-// divide n, one segment.
+// The tiles of one launch over a batch: the full tiles (G interior sites each) of every chain,
+// numbered chain by chain (full_prefix: first full tile of each chain, nchains + 1 entries),
+// and the packed tiles (pack_prefix: first segment of each packed tile, npacked + 1 entries,
+// into segs).  The kernels process the packed tiles first.  A chain of n sites has
+// floor(n / G) full tiles and, when G does not divide n, one segment.
 struct BatchTiles {
   const int32_t *full_prefix;
   const int32_t *pack_prefix;
@@ -85,7 +85,7 @@ struct BlockedJob {
   int packed;                   // 1: the batch's tiles follow `bt`, 0: `tile_prefix`
   int K;                        // steps in this launch
   int G;                        // interior sites per tile
-  int64_t ntiles;               // tiles of k_blocked in the launch (a packed batch's full tiles)
+  int64_t ntiles;               // tiles in the launch (a packed batch: its full tiles, beside bt.npacked)
   const void *sp;               // per-site parameters of a heterogeneous chain, or NULL
   WsHeader *hdr;                // status word (non-finite results, debug bounds checks)
   int64_t total;                // sites in the state buffers
