@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(BlockedBounds<MODEL, V, KAHAN, HET>::threads,
   if (job.nchains == 1) {
     ch = job.one;
   } else {
-    const int ci = find_chain(job.tile_prefix, job.nchains, item);
+    const int ci = find_chain_block(job.tile_prefix, job.nchains, item, smem);
     ch = job.chains[ci];
     tile = item - job.tile_prefix[ci];
     c.kappa = (R)ch.kappa;

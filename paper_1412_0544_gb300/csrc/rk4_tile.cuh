@@ -599,6 +599,18 @@ __device__ __forceinline__ int find_chain(const int32_t *prefix, int nchains, in
   return lo;
 }
 
+// find_chain done once per block: thread 0 searches and passes the answer to the others
+// through the first word of the block's shared memory (the neighbour-exchange area, which the
+// tile kernels first write after the barrier that ends their tile load, when every thread has
+// read the answer).  A dozen dependent loads per tile by one thread instead of by all.
+__device__ __forceinline__ int find_chain_block(const int32_t *prefix, int nchains, int64_t tile,
+                                                unsigned char *smem) {
+  int *slot = reinterpret_cast<int *>(smem);
+  if (threadIdx.x == 0) *slot = find_chain(prefix, nchains, tile);
+  __syncthreads();
+  return *slot;
+}
+
 // Item `item` of a batch launch laid out by bt: the packed tiles first (they then run among the
 // full tiles instead of alone at the end), then the full tiles of the chains.
 template <typename R, int MODEL, int V, bool KAHAN, bool COH>
@@ -611,7 +623,7 @@ __device__ __forceinline__ void batch_item(const R *__restrict__ in, R *__restri
                                               bt.pack_prefix[item + 1], K, cf, smem, sites, hdr);
   } else {
     const int64_t f = item - bt.npacked;
-    const int ci = find_chain(bt.full_prefix, nchains, f);
+    const int ci = find_chain_block(bt.full_prefix, nchains, f, smem);
     const ChainDesc ch = chains[ci];
     Coef<R> c = cf;
     c.kappa = (R)ch.kappa;
