@@ -32,23 +32,22 @@ __device__ __noinline__ void packed_tile_call(const void *in, void *out, const v
                                               pack_prefix[p], pack_prefix[p + 1], K, cf, smem, sites, hdr);
 }
 
-template <typename R, int MODEL, int V, bool KAHAN, bool HET>
+// PACKED: a packed batch's launch (its own instantiation, so that single chains run the plain
+// tile path alone): the packed tiles come first, so that they run in the first wave beside full
+// tiles instead of alone after the last one, then the full tiles with 16-byte-aligned windows.
+template <typename R, int MODEL, int V, bool KAHAN, bool HET, bool PACKED = false>
 __global__ void __launch_bounds__(BlockedBounds<MODEL, V, KAHAN, HET>::threads,
                                   BlockedBounds<MODEL, V, KAHAN, HET>::min_blocks)
     k_blocked(BlockedJob job, Coef<R> cf) {
   extern __shared__ __align__(16) unsigned char smem[];
   int64_t item = blockIdx.x;
-  if constexpr (!HET) {
-    if (job.nchains > 1 && job.packed) {
-      // a packed batch: its packed tiles come first, so that they run in the first wave beside
-      // full tiles instead of alone after the last one
-      if (item < job.bt.npacked) {
-        packed_tile_call<R, MODEL, V, KAHAN>(job.in, job.out, job.cin, job.cout, job.chains, job.bt.segs,
-                                             job.bt.pack_prefix, item, job.K, cf, smem, job.total, job.hdr);
-        return;
-      }
-      item -= job.bt.npacked;
+  if constexpr (PACKED) {
+    if (item < job.bt.npacked) {
+      packed_tile_call<R, MODEL, V, KAHAN>(job.in, job.out, job.cin, job.cout, job.chains, job.bt.segs,
+                                           job.bt.pack_prefix, item, job.K, cf, smem, job.total, job.hdr);
+      return;
     }
+    item -= job.bt.npacked;
   }
   ChainDesc ch;
   int64_t tile = item;
@@ -61,7 +60,7 @@ __global__ void __launch_bounds__(BlockedBounds<MODEL, V, KAHAN, HET>::threads,
     tile = item - job.tile_prefix[ci];
     c.kappa = (R)ch.kappa;
   }
-  tile_item<R, MODEL, V, KAHAN, false, HET>(static_cast<const R *>(job.in), static_cast<R *>(job.out),
+  tile_item<R, MODEL, V, KAHAN, false, HET, PACKED>(static_cast<const R *>(job.in), static_cast<R *>(job.out),
                                             static_cast<const R *>(job.cin), static_cast<R *>(job.cout), ch, tile,
                                             job.K, job.G, c, smem, job.total, job.hdr,
                                             static_cast<const R *>(job.sp));
@@ -76,14 +75,21 @@ size_t blocked_smem_bytes(int model, bool fp32, int v, int block, bool het) {
 
 template <typename R, int MODEL, int V, bool KAHAN, bool HET>
 static cudaError_t launch_one(int block, const BlockedJob &job, const CoefD &cfd, cudaStream_t st) {
-  static PerDevice attr;
-  const cudaError_t attr_err = set_smem_limit_once(k_blocked<R, MODEL, V, KAHAN, HET>, 200 * 1024, attr);
-  if (attr_err != cudaSuccess) return attr_err;
+  static PerDevice attr, attr_p;
   const size_t smem = blocked_smem_bytes(MODEL, KAHAN, V, block, HET);
   Coef<R> cf = to_coef<R>(cfd, cfd.kappa);
-  // one block per full tile and (packed batches) one per packed tile
-  const int64_t grid = job.ntiles + ((!HET && job.nchains > 1 && job.packed) ? job.bt.npacked : 0);
-  if (grid > 0) k_blocked<R, MODEL, V, KAHAN, HET><<<(unsigned)grid, block, smem, st>>>(job, cf);
+  if constexpr (!HET) {
+    if (job.nchains > 1 && job.packed) {  // one block per packed tile and one per full tile
+      const cudaError_t e = set_smem_limit_once(k_blocked<R, MODEL, V, KAHAN, false, true>, 200 * 1024, attr_p);
+      if (e != cudaSuccess) return e;
+      const int64_t grid = job.ntiles + job.bt.npacked;
+      if (grid > 0) k_blocked<R, MODEL, V, KAHAN, false, true><<<(unsigned)grid, block, smem, st>>>(job, cf);
+      return cudaGetLastError();
+    }
+  }
+  const cudaError_t e = set_smem_limit_once(k_blocked<R, MODEL, V, KAHAN, HET>, 200 * 1024, attr);
+  if (e != cudaSuccess) return e;
+  if (job.ntiles > 0) k_blocked<R, MODEL, V, KAHAN, HET><<<(unsigned)job.ntiles, block, smem, st>>>(job, cf);
   return cudaGetLastError();
 }
 

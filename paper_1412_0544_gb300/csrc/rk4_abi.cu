@@ -104,6 +104,8 @@ bool use_generic(const rk4_chain *h);
 
 bool use_het(const rk4_chain *h);
 
+int tile_interior(const rk4_chain *h, int W, int k);
+
 int effective_kernel(const rk4_chain *h) {
   if (h->kernel != RK4_KERNEL_AUTO) return h->kernel;
   if (h->tuned_kernel != 0) return h->tuned_kernel;  // the autotuner's measured choice
@@ -246,7 +248,7 @@ void default_tiling(rk4_chain *h) {
     h->tiling.v = 4;
     h->tiling.k = h->fp32 ? 4 : 1;
   }
-  h->tiling.G = h->tiling.block * h->tiling.v - 2 * halo(h, h->tiling.k);
+  h->tiling.G = tile_interior(h, h->tiling.block * h->tiling.v, h->tiling.k);
 }
 
 int64_t tiles_for(const rk4_chain *h, int G) {
@@ -259,6 +261,24 @@ int64_t tiles_for(const rk4_chain *h, int G) {
 // partial pieces into shared tiles; the generic and heterogeneous kernels give every chain
 // whole tiles of its own.
 bool packed_batch(const rk4_chain *h) { return h->nchains > 1 && !use_generic(h) && !use_het(h); }
+
+// Sites per 16 bytes of state in whole sites: a packed batch's full tiles start their windows at
+// multiples of it (so they move by 16-byte vectors wherever the chain starts), which the interior
+// pays with up to that many sites less than W - 2 H.
+int batch_align(const rk4_chain *h) {
+  int a = h->D * (int)elem_bytes(h), b = 16;
+  while (b) {
+    const int t = a % b;
+    a = b;
+    b = t;
+  }
+  return 16 / a;
+}
+
+// Interior sites per tile for tiles of W sites and k steps.
+int tile_interior(const rk4_chain *h, int W, int k) {
+  return W - 2 * halo(h, k) - (packed_batch(h) ? batch_align(h) - 1 : 0);
+}
 
 
 Plan make_plan(int64_t nsteps, int K) {
@@ -408,7 +428,7 @@ cudaError_t prepare_tables(rk4_chain *h, const std::vector<int> &kval, int W) {
   if (e != cudaSuccess) return e;
   for (size_t i = 0; i < kval.size(); ++i) {
     const int H = halo(h, kval[i]);
-    const int G = W - 2 * H;
+    const int G = tile_interior(h, W, kval[i]);
     KTables t = host_ktables(h, (int)i);
     int64_t acc = 0;
     for (int c = 0; c < h->nchains; ++c) {
@@ -503,7 +523,7 @@ cudaError_t enqueue_integrate(rk4_chain *h, int kernel, void *state, void *comp,
       int ki = 0;
       while (P.kval[ki] != k) ++ki;
       j.K = k;
-      j.G = W - 2 * halo(h, k);
+      j.G = tile_interior(h, W, k);
       if (h->nchains > 1) {
         // ntiles counts the full tiles (or, unpacked, every tile); the packed tiles follow them
         // in the same launch
@@ -538,7 +558,7 @@ cudaError_t enqueue_integrate(rk4_chain *h, int kernel, void *state, void *comp,
     int64_t maxtiles = 0;
     for (int i = 0; i < j.nk; ++i) {
       j.kval[i] = P.kval[i];
-      j.Gval[i] = W - 8 * P.kval[i];
+      j.Gval[i] = tile_interior(h, W, P.kval[i]);
       if (h->nchains > 1) {
         j.bt[i] = dev_ktables(h, ws, L, i);
         j.ntiles[i] = j.bt[i].nfull + j.bt[i].npacked;
@@ -601,7 +621,7 @@ int integrate_impl(rk4_chain *h, void *state, void *comp, void *ws, size_t ws_by
   if (kernel != RK4_KERNEL_STAGED) {
     // tile counts must fit a 1-D grid and the int32 prefix tables
     const int kmax = *std::max_element(P.kval.begin(), P.kval.end());
-    if (tiles_for(h, h->tiling.block * h->tiling.v - 2 * halo(h, kmax)) > 0x7fffffffLL) return RK4_EUNSUPPORTED;
+    if (tiles_for(h, tile_interior(h, h->tiling.block * h->tiling.v, kmax)) > 0x7fffffffLL) return RK4_EUNSUPPORTED;
   }
   if (prepare_tables(h, P.kval, h->tiling.block * h->tiling.v) != cudaSuccess) return RK4_ECUDA;
   char *w = static_cast<char *>(ws);
@@ -821,7 +841,7 @@ int rk4_chain_set_tiling(rk4_chain *h, int block, int v, int k) {
   h->tiling.block = block;
   h->tiling.v = v;
   h->tiling.k = k;
-  h->tiling.G = block * v - 2 * halo(h, k);
+  h->tiling.G = tile_interior(h, block * v, k);
   return RK4_OK;
 }
 
@@ -962,7 +982,7 @@ int rk4_debug_barrier_timeout(rk4_chain *h, void *state, void *comp, void *ws, s
   j.nk = 1;
   j.kval[0] = h->tiling.k;
   if (use_generic(h)) return RK4_EUNSUPPORTED;
-  j.Gval[0] = W - 8 * h->tiling.k;
+  j.Gval[0] = tile_interior(h, W, h->tiling.k);
   if (h->nchains > 1) {
     j.bt[0] = dev_ktables(h, w, L, 0);
     j.ntiles[0] = j.bt[0].nfull + j.bt[0].npacked;
@@ -1057,7 +1077,7 @@ int rk4_chain_autotune(rk4_chain *h, void *state, void *comp, void *ws, size_t w
           h->tiling.block = b;
           h->tiling.v = v;
           h->tiling.k = k;
-          h->tiling.G = b * v - 2 * halo(h, k);
+          h->tiling.G = tile_interior(h, b * v, k);
           const int64_t steps = ((probe_steps + 2 * k - 1) / (2 * k)) * 2 * k;  // whole, even launch count
           const float per_step = time_steps(2 * k, steps);
           if (per_step >= 0.f && per_step < best_ms) {

@@ -263,6 +263,28 @@ __device__ __forceinline__ void copy_out(R *__restrict__ dst, const R *src, int 
     for (int e = threadIdx.x; e < count; e += blockDim.x) dst[e] = src[e];
   }
 }
+// copy_out for a range whose shared-memory side sits at the same 16-byte offset as its global
+// side (the interior of a batch tile whose window starts on a 16-byte boundary): the values
+// before the first and after the last whole vector singly, the rest by 16-byte vectors on both
+// sides.  Any other range is copied singly.
+template <typename R>
+__device__ __forceinline__ void copy_out_matched(R *__restrict__ dst, const R *src, int count) {
+  constexpr int kPer = 16 / (int)sizeof(R);
+  const unsigned md = (unsigned)(reinterpret_cast<uintptr_t>(dst) & 15u);
+  if (md != (unsigned)(reinterpret_cast<uintptr_t>(src) & 15u)) {
+    for (int e = threadIdx.x; e < count; e += blockDim.x) dst[e] = src[e];
+    return;
+  }
+  int head = (int)(((16u - md) & 15u) / sizeof(R));
+  if (head > count) head = count;
+  const int nv = (count - head) / kPer;
+  for (int e = threadIdx.x; e < head; e += blockDim.x) dst[e] = src[e];
+  int4 *d4 = reinterpret_cast<int4 *>(dst + head);
+  const int4 *s4 = reinterpret_cast<const int4 *>(src + head);
+  for (int e = threadIdx.x; e < nv; e += blockDim.x) d4[e] = s4[e];
+  for (int e = head + nv * kPer + threadIdx.x; e < count; e += blockDim.x) dst[e] = src[e];
+}
+
 template <bool COH, typename R>
 __device__ __forceinline__ void copy_in_vec(R *dst, const R *__restrict__ src, int count) {
   constexpr int kPer = 16 / (int)sizeof(R);
@@ -407,21 +429,38 @@ __device__ __forceinline__ void tile_load_async(R *tile, const R *__restrict__ s
 }
 
 // Store `cnt` sites of the tile starting at tile-local site `first` to chain index g0 (VEC:
-// copy_out_vec, for the persistent kernel).
-template <typename R, int D, bool VEC = false>
+// copy_out_vec, for the persistent kernel; MATCHED: copy_out_matched, for tiles whose window
+// starts on a 16-byte boundary).
+template <typename R, int D, bool VEC = false, bool MATCHED = false>
 __device__ __forceinline__ void tile_store(R *__restrict__ dst, const R *tile, int64_t off, int first, int64_t g0,
                                            int cnt, int64_t sites, int W, WsHeader *hdr) {
   if (!bounds_ok(hdr, in_range(off + g0, cnt, sites) && in_range(first, cnt, W))) return;
-  if constexpr (VEC) copy_out_vec(dst + (off + g0) * D, tile + first * D, cnt * D);
+  if constexpr (MATCHED) copy_out_matched(dst + (off + g0) * D, tile + first * D, cnt * D);
+  else if constexpr (VEC) copy_out_vec(dst + (off + g0) * D, tile + first * D, cnt * D);
   else copy_out(dst + (off + g0) * D, tile + first * D, cnt * D);
 }
 
+// Sites per 16 bytes of a [sites][D] array of R, in whole sites (16 / gcd(16, D sizeof(R))).
+template <typename R, int D> __host__ __device__ constexpr int align_sites() {
+  int a = D * (int)sizeof(R), b = 16;
+  while (b) {
+    const int t = a % b;
+    a = b;
+    b = t;
+  }
+  return 16 / a;
+}
+
 // Process one (chain, tile) item end to end: load, advance K steps, store the interior.
+// ALN (batch tiles): the window starts at the last multiple of align_sites() at or before
+// tile G - H in the state array, so it moves by whole 16-byte vectors wherever the chain
+// starts; the left halo is then H .. H + A - 1 sites, and the host shrinks G by A - 1 so that
+// the right halo keeps at least H.
 // Shared memory: edge[edge_values(V)] | tile[W*D] | ctile[W*D] (Kahan) | ptile[W*P]
 // (heterogeneous).
 // `sites` is the number of sites in the state buffers (for the debug bounds checks); hdr the
 // status word, where a non-finite stored value is reported.
-template <typename R, int MODEL, int V, bool KAHAN, bool COH, bool HET = false>
+template <typename R, int MODEL, int V, bool KAHAN, bool COH, bool HET = false, bool ALN = false>
 __device__ __forceinline__ void tile_item(const R *__restrict__ in, R *__restrict__ out, const R *__restrict__ cin,
                                           R *__restrict__ cout, const ChainDesc &ch, int64_t tile, int K, int G,
                                           const Coef<R> &cf, unsigned char *smem, int64_t sites, WsHeader *hdr,
@@ -431,7 +470,14 @@ __device__ __forceinline__ void tile_item(const R *__restrict__ in, R *__restric
   R *edge = reinterpret_cast<R *>(smem);
   const int W = blockDim.x * V;
   const int H = 4 * K;
-  const int64_t t0 = tile * (int64_t)G - H;
+  const int64_t g0 = tile * (int64_t)G;  // first interior site
+  int64_t t0 = g0 - H;
+  if constexpr (ALN) {
+    constexpr int A = align_sites<R, D>();
+    const int64_t a = ch.off + t0;  // rounded down (toward minus infinity) to a multiple of A
+    t0 = (a >= 0 ? a / A : -((-a + A - 1) / A)) * A - ch.off;
+  }
+  const int hl = (int)(g0 - t0);  // left halo: H, or up to A - 1 sites more with ALN
   R *tl = edge + edge_values(V);
   R *ctl = tl + W * D;
   R *ptl = ctl + (KAHAN ? W * D : 0);
@@ -470,13 +516,12 @@ __device__ __forceinline__ void tile_item(const R *__restrict__ in, R *__restric
     tile_advance<R, MODEL, V, KAHAN, false, HET>(y, cmp, 0u, K, cf, edge, cs);
   }
 
-  const int64_t g0 = t0 + H;  // = tile * G
   const int64_t rem = ch.n - g0;
   const int cnt = (int)(rem < G ? rem : G);
   bool bad = false;  // a stored (interior) value is NaN or infinite
 #pragma unroll
   for (int v = 0; v < V; ++v) {
-    const bool stored = base + v >= H && base + v < H + cnt;
+    const bool stored = base + v >= hl && base + v < hl + cnt;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       tl[(base + v) * D + d] = y[v][d];
@@ -486,8 +531,8 @@ __device__ __forceinline__ void tile_item(const R *__restrict__ in, R *__restric
   }
   report_nonfinite(hdr, __syncthreads_or(bad));
   if (cnt > 0) {
-    tile_store<R, D, COH>(out, tl, ch.off, H, g0, cnt, sites, W, hdr);
-    if constexpr (KAHAN) tile_store<R, D, COH>(cout, ctl, ch.off, H, g0, cnt, sites, W, hdr);
+    tile_store<R, D, COH, ALN>(out, tl, ch.off, hl, g0, cnt, sites, W, hdr);
+    if constexpr (KAHAN) tile_store<R, D, COH, ALN>(cout, ctl, ch.off, hl, g0, cnt, sites, W, hdr);
   }
   __syncthreads();  // shared memory is reused by the next item
 }
@@ -627,7 +672,8 @@ __device__ __forceinline__ void batch_item(const R *__restrict__ in, R *__restri
     const ChainDesc ch = chains[ci];
     Coef<R> c = cf;
     c.kappa = (R)ch.kappa;
-    tile_item<R, MODEL, V, KAHAN, COH>(in, out, cin, cout, ch, f - bt.full_prefix[ci], K, G, c, smem, sites, hdr);
+    tile_item<R, MODEL, V, KAHAN, COH, false, true>(in, out, cin, cout, ch, f - bt.full_prefix[ci], K, G, c, smem,
+                                                    sites, hdr);
   }
 }
 
