@@ -278,8 +278,12 @@ def fp32_kahan_extra(rk, torch, stream, n=1 << 27, nsteps=NSTEPS):
                     "fp32_pipe_frac_of_measured": sps * FP32K_INST_PER_SITE_STEP / FP32_INST_PEAK,
                     "ms_per_launch": 1e3 * el / launches, "half_norm2_t0": e32_0, "half_norm2_fp32": e32})
         if "rk4_fp32k_regs_lane_ops_per_s" in PROBE:
-            # against the same packed instruction stream on register-resident sites
+            # against the same packed instruction stream on register-resident sites (4 sites per
+            # thread; with 8, twice the independent work per thread)
             out["frac_of_arithmetic_only"] = sps * FP32K_INST_PER_SITE_STEP / PROBE["rk4_fp32k_regs_lane_ops_per_s"]
+            if "rk4_fp32k_regs_v8_lane_ops_per_s" in PROBE:
+                out["frac_of_arithmetic_only_v8"] = (sps * FP32K_INST_PER_SITE_STEP /
+                                                     PROBE["rk4_fp32k_regs_v8_lane_ops_per_s"])
         del st, cp, ws
     finally:
         rk.rk4_chain_destroy(h)
@@ -795,14 +799,21 @@ def main():
     dev2 = torch.empty_like(st)
     rk.rk4_chain_integrate_host(h, host, None, dev2, None, ws, nsteps)  # warm
     dist.barrier()
-    t0 = time.perf_counter()
     e2e_steps = 2
-    for _ in range(e2e_steps):
-        rk.rk4_chain_integrate_host(h, host, None, dev2, None, ws, nsteps)
-    el_e2e = dist.max_over_ranks(time.perf_counter() - t0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with ClockSampler(local) as e2e_clocks:
+        t0 = time.perf_counter()
+        ev[0].record(stream)
+        for _ in range(e2e_steps):
+            rk.rk4_chain_integrate_host(h, host, None, dev2, None, ws, nsteps)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        el_e2e = dist.max_over_ranks(time.perf_counter() - t0)
     e2e = {"value": float(n) * nsteps * e2e_steps * world / el_e2e, "unit": "site-steps/s",
            "h2d_bytes_per_step": n * D * 8, "d2h_bytes_per_step": n * D * 8,
-           "api": "rk4_chain_integrate_host (pinned host state in, result out)"}
+           "api": "rk4_chain_integrate_host (pinned host state in, result out)",
+           "device_s_per_step": ev[0].elapsed_time(ev[1]) / 1e3 / e2e_steps,
+           "wall_s_per_step": el_e2e / e2e_steps, "clocks": e2e_clocks.summary()}
     del host, dev2
 
     extras = {}

@@ -276,6 +276,9 @@ int main() {
   const double rk4_fp64 = rate(rk4_regs_fp64<4>, sms, 512, 4 * 49, out);
   const double rk4_fp64_rt = rate(rk4_regs_fp64<4, true>, sms, 512, 4 * 49, out);
   const double rk4_fp32k = rate(rk4_regs_fp32k<4>, sms, 4096, 4 * 58, out);
+  // twice the independent site pairs per thread: how much of the stream's gap to the FMA rate is
+  // dependency latency rather than the operation mix
+  const double rk4_fp32k_v8 = rate(rk4_regs_fp32k<8>, sms, 2048, 8 * 58, out);
 
   // bit check on 2^20 operands per input, spread over many binades and both signs
   const int n = 1 << 20;
@@ -330,9 +333,10 @@ int main() {
          "\"ffma_scalar_16chains_per_s\": %.5g, \"ffma_packed_8lanes_per_s\": %.5g, "
          "\"ffma_packed_16lanes_per_s\": %.5g, \"packed_vs_scalar_fma_mismatches\": %d, "
          "\"packed_bit_check_values\": %d, \"copy_gbs\": %.1f, \"rk4_fp64_regs_inst_per_s\": %.5g, "
-         "\"rk4_fp32k_regs_lane_ops_per_s\": %.5g, \"rk4_fp64_regs_smem_roundtrip_inst_per_s\": %.5g}\n",
+         "\"rk4_fp32k_regs_lane_ops_per_s\": %.5g, \"rk4_fp32k_regs_v8_lane_ops_per_s\": %.5g, "
+         "\"rk4_fp64_regs_smem_roundtrip_inst_per_s\": %.5g}\n",
          sms, clk_khz / 1e3, dfma, dadd, dmul, dmix, d3reg, ffma8, ffma16, ffma2_4, ffma2_8, mismatches, n, best_gbs,
-         rk4_fp64, rk4_fp32k, rk4_fp64_rt);
+         rk4_fp64, rk4_fp32k, rk4_fp32k_v8, rk4_fp64_rt);
   free(h);
   return mismatches == 0 ? 0 : 2;
 }
