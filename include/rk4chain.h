@@ -204,7 +204,10 @@ int rk4_chain_integrate(rk4_chain *h, void *state, void *comp, void *ws, size_t 
 
 /* The same starting from and returning to HOST buffers: copies host_state (and host_comp)
  * into the device buffers dev_state (dev_comp), integrates, copies the result back and
- * synchronises the stream.  Pinned host memory gives asynchronous copies. */
+ * synchronises the stream.  The host buffers hold the whole state ([N][D] values of the
+ * handle's precision).  Page-locked (pinned) host memory that the device can address, 16-byte
+ * aligned, is read and written by a copy kernel through its device address; any other host
+ * memory goes through cudaMemcpyAsync. */
 int rk4_chain_integrate_host(rk4_chain *h, void *host_state, void *host_comp, void *dev_state,
                              void *dev_comp, void *ws, size_t ws_bytes, int64_t nsteps, double *t);
 

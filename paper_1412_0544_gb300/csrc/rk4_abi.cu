@@ -694,6 +694,28 @@ rk4_chain *new_handle(int model, int precision, double dt, const rk4_params *p, 
   return h;
 }
 
+// Device address of page-locked host memory that the device can access, or NULL (pageable
+// memory, or memory the runtime does not know).
+void *mapped_host(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the error of the query
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return nullptr;
+  // the device address of this very byte (the query names the start of p's allocation)
+  return static_cast<char *>(a.devicePointer) + (static_cast<const char *>(p) - static_cast<const char *>(a.hostPointer));
+}
+
+// One host <-> device transfer of integrate_host: by the SMs when the host buffer is mapped
+// page-locked memory and both sides are 16-byte aligned (k_copy.cu), else by cudaMemcpyAsync.
+cudaError_t host_transfer(void *dst, const void *src, size_t bytes, bool to_device, cudaStream_t st) {
+  void *hd = mapped_host(to_device ? src : dst);
+  if (hd && ((reinterpret_cast<uintptr_t>(hd) | reinterpret_cast<uintptr_t>(to_device ? dst : src)) & 15u) == 0)
+    return to_device ? launch_copy(dst, hd, bytes, st) : launch_copy(hd, src, bytes, st);
+  return cudaMemcpyAsync(dst, src, bytes, to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost, st);
+}
+
 }  // namespace
 
 // Read-only view of a handle for the allocation-free reduction entry point.
@@ -886,14 +908,12 @@ int rk4_chain_integrate_host(rk4_chain *h, void *host_state, void *host_comp, vo
   if (rc) return rc;
   if (ws_bytes < layout(h, effective_kernel(h)).total) return RK4_ENOMEM_WS;
   const size_t bytes = (size_t)h->total * h->D * elem_bytes(h);
-  if (cudaMemcpyAsync(dev_state, host_state, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) return RK4_ECUDA;
-  if (h->fp32 && cudaMemcpyAsync(dev_comp, host_comp, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
-    return RK4_ECUDA;
+  if (host_transfer(dev_state, host_state, bytes, true, h->stream) != cudaSuccess) return RK4_ECUDA;
+  if (h->fp32 && host_transfer(dev_comp, host_comp, bytes, true, h->stream) != cudaSuccess) return RK4_ECUDA;
   rc = rk4_chain_integrate(h, dev_state, dev_comp, ws, ws_bytes, nsteps, t);
   if (rc) return rc;
-  if (cudaMemcpyAsync(host_state, dev_state, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return RK4_ECUDA;
-  if (h->fp32 && cudaMemcpyAsync(host_comp, dev_comp, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
-    return RK4_ECUDA;
+  if (host_transfer(host_state, dev_state, bytes, false, h->stream) != cudaSuccess) return RK4_ECUDA;
+  if (h->fp32 && host_transfer(host_comp, dev_comp, bytes, false, h->stream) != cudaSuccess) return RK4_ECUDA;
   return cudaStreamSynchronize(h->stream) == cudaSuccess ? RK4_OK : RK4_ECUDA;
 }
 

@@ -164,6 +164,9 @@ struct GhostPair {
 // compensation; rows are row_bytes (a multiple of 4) long.
 cudaError_t launch_ghost_copy(void *state, void *comp, const GhostPair *pairs, int npairs, int64_t ghost,
                               int row_bytes, cudaStream_t st);
+// Copy `bytes` between two 16-byte-aligned buffers with a kernel (either side may be mapped
+// page-locked host memory, given by its device pointer).
+cudaError_t launch_copy(void *dst, const void *src, size_t bytes, cudaStream_t st);
 cudaError_t launch_fill_uniform(void *dst, int64_t count, uint64_t seed, uint64_t start, bool fp32,
                                 cudaStream_t st);
 cudaError_t launch_gen_staged_step(int model, bool fp32, int range, const GenStagedJob &job, const CoefD &cf,

@@ -337,17 +337,33 @@ def test_time_bookkeeping(rk):
     rk.rk4_chain_destroy(h)
 
 
-def test_integrate_host_buffers(rk, gh):
+@pytest.mark.parametrize("pinned", [True, False])
+def test_integrate_host_buffers(rk, gh, pinned):
+    """Host buffers in and out: page-locked memory moves by the library's copy kernel, pageable
+    memory by cudaMemcpyAsync; an odd number of bytes leaves a tail the copy kernel moves
+    singly (the harmonic chain of 20001 sites holds 320016 bytes, FP32-Kahan 160008)."""
     import torch
-    y0 = ci.uniform_state(20000, 3, seed=97)
-    ref = gh.gpu_run(y0, nsteps=30)
-    h = rk.rk4_chain_create(ROE, rk.RK4_FP64, y0.shape[0], 0.01, PER)
-    host = torch.from_numpy(y0.copy()).pin_memory()
-    dev = torch.empty_like(host, device="cuda")
-    ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
-    rk.rk4_chain_integrate_host(h, host, None, dev, None, ws, 30)
-    assert np.array_equal(host.numpy(), ref)
-    rk.rk4_chain_destroy(h)
+    for model, prec, n in ((ROE, rk.RK4_FP64, 20000), (HAR, rk.RK4_FP64, 20001), (ROE, rk.RK4_FP32_KAHAN, 20003)):
+        D = 3 if model == ROE else 2
+        fp32 = prec == rk.RK4_FP32_KAHAN
+        y0 = ci.uniform_state(n, D, seed=97)
+        if fp32:
+            y0 = y0.astype(np.float32)
+        ref, cref = gh.gpu_run(y0, model=model, precision=prec, nsteps=30, return_comp=True)
+        h = rk.rk4_chain_create(model, prec, n, 0.01, PER)
+        host = torch.from_numpy(y0.copy())
+        hcomp = torch.zeros_like(host) if fp32 else None
+        if pinned:
+            host = host.pin_memory()
+            hcomp = hcomp.pin_memory() if fp32 else None
+        dev = torch.empty_like(host, device="cuda")
+        dcomp = torch.empty_like(host, device="cuda") if fp32 else None
+        ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+        rk.rk4_chain_integrate_host(h, host, hcomp, dev, dcomp, ws, 30)
+        assert np.array_equal(host.double().numpy(), ref), (model, prec)
+        if fp32:
+            assert np.array_equal(hcomp.double().numpy(), cref)
+        rk.rk4_chain_destroy(h)
 
 
 def test_batch_autotune_chooses_scheme_and_stays_bitwise(rk, gh, small_batch):
