@@ -402,8 +402,10 @@ def size_sweep(args):
     import paper_1412_0544_gb300 as rk
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
+    # "autotuned": RK4_KERNEL_AUTO with a workspace large enough for the staged scheme too, so
+    # that rk4_chain_autotune picks the faster of the tiled and the standard scheme
     schemes = [("standard", rk.RK4_KERNEL_STAGED), ("blocked", rk.RK4_KERNEL_BLOCKED),
-               ("persistent", rk.RK4_KERNEL_PERSISTENT)]
+               ("persistent", rk.RK4_KERNEL_PERSISTENT), ("autotuned", rk.RK4_KERNEL_AUTO)]
     lo, hi = args.sweep_min, args.sweep_max
     tuned = {}  # the paper finds the optimal cluster size independent of N: tune up to 2^22, then reuse
     for p in range(lo, hi + 1):
@@ -418,9 +420,18 @@ def size_sweep(args):
                     rk.rk4_chain_set_kernel(h, kern)
                     st = st0.clone()
                     cp = torch.zeros_like(st) if prec == rk.RK4_FP32_KAHAN else None
-                    ws = torch.empty(rk.rk4_chain_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+                    wsb = rk.rk4_chain_workspace_bytes(h)
+                    if kern == rk.RK4_KERNEL_AUTO:
+                        rk.rk4_chain_set_kernel(h, rk.RK4_KERNEL_STAGED)
+                        wsb = max(wsb, rk.rk4_chain_workspace_bytes(h))
+                        rk.rk4_chain_set_kernel(h, rk.RK4_KERNEL_AUTO)
+                    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
                     tiling = None
-                    if kern != rk.RK4_KERNEL_STAGED:
+                    if kern == rk.RK4_KERNEL_AUTO:
+                        tiling = rk.rk4_chain_autotune(h, st.clone(), cp.clone() if cp is not None else None, ws, 32)
+                        tiling["kernel"] = {rk.RK4_KERNEL_STAGED: "standard", rk.RK4_KERNEL_BLOCKED: "blocked",
+                                            rk.RK4_KERNEL_PERSISTENT: "persistent"}[rk.rk4_chain_get_kernel(h)]
+                    elif kern != rk.RK4_KERNEL_STAGED:
                         if p <= 22 or (pname, sname) not in tuned:
                             tiling = rk.rk4_chain_autotune(h, st.clone(), cp.clone() if cp is not None else None,
                                                            ws, 32)

@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(GenBounds<R, V, SHAPE>::threads) k_gen_blocked
       ch = job.one;
       tile = it;
     } else {
-      const int ci = find_chain(job.tile_prefix, job.nchains, it);
+      const int ci = find_chain_warp(job.tile_prefix, job.nchains, it);  // every warp, three rounds of loads
       ch = job.chains[ci];
       tile = it - job.tile_prefix[ci];
       c.kappa = (R)ch.kappa;

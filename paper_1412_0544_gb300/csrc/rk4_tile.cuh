@@ -644,14 +644,34 @@ __device__ __forceinline__ int find_chain(const int32_t *prefix, int nchains, in
   return lo;
 }
 
-// find_chain done once per block: thread 0 searches and passes the answer to the others
-// through the first word of the block's shared memory (the neighbour-exchange area, which the
-// tile kernels first write after the barrier that ends their tile load, when every thread has
-// read the answer).  A dozen dependent loads per tile by one thread instead of by all.
+// find_chain by one warp: each round the 32 lanes test 32 evenly spaced candidates at once and
+// the range shrinks 32-fold, so 4096 chains take three rounds of loads instead of twelve
+// dependent ones.  Call with all 32 lanes of a warp; every lane returns the answer.
+__device__ __forceinline__ int find_chain_warp(const int32_t *prefix, int nchains, int64_t tile) {
+  const int lane = threadIdx.x & 31;
+  int lo = 0, hi = nchains - 1;  // the answer (largest c with prefix[c] <= tile) lies in [lo, hi]
+  while (hi > lo) {
+    const int step = (hi - lo + 32) / 32;  // ceil((hi - lo + 1) / 32)
+    const int c = lo + lane * step;
+    const unsigned ok = __ballot_sync(kFull, c <= hi && prefix[c] <= tile);
+    const int last = 31 - __clz(ok);  // lane 0's candidate, lo, always qualifies
+    lo += last * step;
+    hi = min(hi, lo + step - 1);
+  }
+  return lo;
+}
+
+// The chain of a batch tile, found once per block: the first warp searches (find_chain_warp)
+// and passes the answer to the others through the first word of the block's shared memory (the
+// neighbour-exchange area, which the tile kernels first write after the barrier that ends
+// their tile load, when every thread has read the answer).
 __device__ __forceinline__ int find_chain_block(const int32_t *prefix, int nchains, int64_t tile,
                                                 unsigned char *smem) {
   int *slot = reinterpret_cast<int *>(smem);
-  if (threadIdx.x == 0) *slot = find_chain(prefix, nchains, tile);
+  if (threadIdx.x < 32) {
+    const int c = find_chain_warp(prefix, nchains, tile);
+    if (threadIdx.x == 0) *slot = c;
+  }
   __syncthreads();
   return *slot;
 }
