@@ -162,7 +162,9 @@ __device__ __forceinline__ void gen_tile_advance(R (&y)[V][Dim<MODEL>::D], R (&c
       tv.y = ext[V + 1];
       head[tid] = hv;
       tail[tid] = tv;
-      __syncthreads();
+      // each thread reads only its neighbour threads' slots: the streaming form (at most 512
+      // threads) waits for the neighbouring warps only
+      if constexpr (SHAPE != 0) neighbour_warp_sync(); else __syncthreads();
       {
         const R2 l = tail[lt];
         const R2 r = head[rt];

@@ -102,6 +102,28 @@ __device__ __forceinline__ void ld_shared(unsigned a, double &v) {
   asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
 }
 
+// Synchronise this warp with its two neighbouring warps only, for a neighbour exchange in
+// which each thread reads the slots of the threads just before and after it: one named barrier
+// per pair of adjacent warps (ids 1 .. 15, 64 threads each; id 0 is __syncthreads), so a warp
+// waits for its neighbours rather than for the slowest warp of the block.  Warp w takes the
+// barrier it shares with w - 1 and then the one it shares with w + 1; the chain starting at
+// warp 0 (which has no left barrier) completes every pair, so no warp waits forever.  The
+// barriers also order the shared-memory accesses of the threads of each warp.  Needs a block of
+// at most 16 warps (512 threads), every thread of a warp taking part.
+__device__ __forceinline__ void neighbour_warp_sync() {
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (nw > 16) {  // more pairs than named barriers: the whole block instead (block-uniform)
+    __syncthreads();
+    return;
+  }
+  if (nw == 1) {
+    __syncwarp();
+    return;
+  }
+  if (w > 0) asm volatile("bar.sync %0, 64;" ::"r"(w) : "memory");
+  if (w < nw - 1) asm volatile("bar.sync %0, 64;" ::"r"(w + 1) : "memory");
+}
+
 // Advance the registers of one tile by K steps.  `edge` is edge_values(V) values of shared
 // memory, two alternating slots by stage parity.  Per-thread exchange (thread_exchange(V)): a
 // slot is [first x of each thread | last x of each thread], strided by the compile-time
