@@ -124,6 +124,13 @@ __device__ __forceinline__ void neighbour_warp_sync() {
   if (w < nw - 1) asm volatile("bar.sync %0, 64;" ::"r"(w + 1) : "memory");
 }
 
+// The barrier of a tile kernel's neighbour exchange, where each thread (warp) reads only the
+// slots of its neighbours: FP64 waits for the neighbouring warps only (neighbour_warp_sync);
+// FP32, bound by instruction issue, keeps the one block-wide barrier per stage.
+template <typename R> __device__ __forceinline__ void stage_sync() {
+  if constexpr (sizeof(R) == 8) neighbour_warp_sync(); else __syncthreads();
+}
+
 // Advance the registers of one tile by K steps.  `edge` is edge_values(V) values of shared
 // memory, two alternating slots by stage parity.  Per-thread exchange (thread_exchange(V)): a
 // slot is [first x of each thread | last x of each thread], strided by the compile-time
@@ -179,7 +186,7 @@ __device__ __forceinline__ void tile_advance(R (&y)[V][Dim<MODEL>::D], R (&cmp)[
         const unsigned po = (j & 1) * 2 * NT * (unsigned)sizeof(R);  // the stage's parity slot
         st_shared(my_first + po, xs[0]);
         st_shared(my_last + po, xs[V - 1]);
-        __syncthreads();
+        stage_sync<R>();
         ld_shared(left_last + po, left);
         ld_shared(right_first + po, right);
       } else {
@@ -188,7 +195,7 @@ __device__ __forceinline__ void tile_advance(R (&y)[V][Dim<MODEL>::D], R (&cmp)[
         R *eb = edge + (j & 1) * 64;  // [0,32): first x of each warp, [32,64): last x
         st_shared_if(is_first, eb + warp, xs[0]);
         st_shared_if(is_last, eb + 32 + warp, xs[V - 1]);
-        __syncthreads();
+        stage_sync<R>();
         const R from_prev = eb[32 + prev];
         const R from_next = eb[next];
         left = is_first ? from_prev : left;
