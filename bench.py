@@ -81,7 +81,7 @@ FP32K_INST_PER_SITE_STEP = 58    # the update: 4 operations per component instea
 # tiling recorded with it; any other combination reports null.  A launch's traffic is
 # proportional to the sites it advances (one read and one write of each tile), so a capture at
 # N = 2^24 scales to the N = 2^27 workload by the site count.
-TRAFFIC = {("5dce9c7b740c9050", "256,4,1"): (402742272 + 357057536, 1 << 24)}
+TRAFFIC = {}
 
 
 def traffic_per_launch(khash: str, tiling: dict, n: int):

@@ -55,15 +55,31 @@ __global__ void __launch_bounds__(BlockedBounds<MODEL, V, KAHAN, HET>::threads,
   if (job.nchains == 1) {
     ch = job.one;
   } else {
-    const int ci = find_chain_block(job.tile_prefix, job.nchains, item, smem);
+    const int ci = batch_chain(job.bt, job.nchains, item, smem, tile);
     ch = job.chains[ci];
-    tile = item - job.tile_prefix[ci];
     c.kappa = (R)ch.kappa;
   }
   tile_item<R, MODEL, V, KAHAN, false, HET, PACKED>(static_cast<const R *>(job.in), static_cast<R *>(job.out),
                                             static_cast<const R *>(job.cin), static_cast<R *>(job.cout), ch, tile,
                                             job.K, job.G, c, smem, job.total, job.hdr,
                                             static_cast<const R *>(job.sp));
+}
+
+// The tile table of a batch launch: tile t's chain (the largest c with prefix[c] <= t, so
+// chains without tiles are skipped) and its index within the chain.
+__global__ void k_tile_chains(const int32_t *__restrict__ prefix, int nchains, int64_t ntiles,
+                              int2 *__restrict__ tile_chain) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
+    const int c = find_chain(prefix, nchains, t);
+    tile_chain[t] = make_int2(c, (int)(t - prefix[c]));
+  }
+}
+
+cudaError_t launch_tile_chains(const int32_t *prefix, int nchains, int64_t ntiles, int2 *tile_chain, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((ntiles + 255) / 256, (int64_t)sm_count() * 8);
+  k_tile_chains<<<(unsigned)blocks, 256, 0, st>>>(prefix, nchains, ntiles, tile_chain);
+  return cudaGetLastError();
 }
 
 size_t blocked_smem_bytes(int model, bool fp32, int v, int block, bool het) {

@@ -221,9 +221,16 @@ __global__ void __launch_bounds__(GenBounds<R, V, SHAPE>::threads) k_gen_blocked
       ch = job.one;
       tile = it;
     } else {
-      const int ci = find_chain_warp(job.tile_prefix, job.nchains, it);  // every warp, three rounds of loads
+      int ci;
+      if (job.bt.tile_chain) {
+        const int2 tc = __ldg(&job.bt.tile_chain[it]);
+        ci = tc.x;
+        tile = tc.y;
+      } else {
+        ci = find_chain_warp(job.bt.full_prefix, job.nchains, it);  // every warp, three rounds of loads
+        tile = it - job.bt.full_prefix[ci];
+      }
       ch = job.chains[ci];
-      tile = it - job.tile_prefix[ci];
       c.kappa = (R)ch.kappa;
     }
   };

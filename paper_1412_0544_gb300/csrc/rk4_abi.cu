@@ -38,7 +38,7 @@ struct GraphKey {
 };
 
 struct WsLayout {
-  size_t hdr, partials, result, chains, prefix, state, comp, u0, u1, acc, total;
+  size_t hdr, partials, result, chains, prefix, tiles, state, comp, u0, u1, acc, total;
 };
 
 // One launch plan: the k of every launch (or time block) and whether the result needs copying
@@ -162,6 +162,11 @@ size_t ktable_bytes(int nchains) {
   return align_up(sizeof(int32_t) * (size_t)(nchains + 1)) * 2 + align_up(sizeof(SegDesc) * (size_t)nchains);
 }
 
+// Entries of one k slot's tile table (the chain of each full tile): room for tiles of at least
+// kTileTableMinG interior sites; a launch with more tiles than that searches the prefix instead.
+constexpr int kTileTableMinG = 64;
+int64_t tile_table_entries(const rk4_chain *h) { return h->total / kTileTableMinG + h->nchains; }
+
 WsLayout layout(const rk4_chain *h, int kernel) {
   WsLayout L{};
   size_t o = 0;
@@ -175,6 +180,8 @@ WsLayout layout(const rk4_chain *h, int kernel) {
   L.result = take(sizeof(double) * (size_t)h->nchains);
   L.chains = take(h->nchains > 1 ? sizeof(ChainDesc) * (size_t)h->nchains : 0);
   L.prefix = take(h->nchains > 1 ? ktable_bytes(h->nchains) * kMaxDistinctK : 0);
+  L.tiles = take(h->nchains > 1 && kernel != RK4_KERNEL_STAGED
+                     ? sizeof(int2) * (size_t)tile_table_entries(h) * kMaxDistinctK : 0);
   const size_t sz = (size_t)h->total * (size_t)h->D * elem_bytes(h);
   L.state = L.comp = L.u0 = L.u1 = L.acc = 0;
   if (kernel == RK4_KERNEL_STAGED && use_generic(h)) {
@@ -353,7 +360,24 @@ BatchTiles dev_ktables(const rk4_chain *h, const char *ws, const WsLayout &L, in
   bt.segs = reinterpret_cast<const SegDesc *>(p + 2 * pre);
   bt.nfull = h->nfull[ki];
   bt.npacked = h->npacked[ki];
+  const int64_t entries = tile_table_entries(h);
+  bt.tile_chain = L.tiles && bt.nfull <= entries
+                      ? reinterpret_cast<const int2 *>(ws + L.tiles + sizeof(int2) * (size_t)entries * (size_t)ki)
+                      : nullptr;
   return bt;
+}
+
+// Fill the tile tables of the first nslots k slots on the device (after upload_tables).
+cudaError_t fill_tile_tables(const rk4_chain *h, char *ws, const WsLayout &L, int nslots, cudaStream_t st) {
+  if (h->nchains == 1) return cudaSuccess;
+  for (int i = 0; i < nslots; ++i) {
+    const BatchTiles bt = dev_ktables(h, ws, L, i);
+    if (!bt.tile_chain) continue;
+    const cudaError_t e =
+        launch_tile_chains(bt.full_prefix, h->nchains, bt.nfull, const_cast<int2 *>(bt.tile_chain), st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // Pack the segments of one k slot into tiles of W slots: each chain's last partial piece of
@@ -509,6 +533,8 @@ cudaError_t enqueue_integrate(rk4_chain *h, int kernel, void *state, void *comp,
   }
   void *wsS = ws + L.state;
   void *wsC = h->fp32 ? (void *)(ws + L.comp) : nullptr;
+  e = fill_tile_tables(h, ws, L, (int)P.kval.size(), st);
+  if (e != cudaSuccess) return e;
   if (kernel == RK4_KERNEL_BLOCKED) {
     BlockedJob j{};
     j.nchains = h->nchains;
@@ -528,7 +554,6 @@ cudaError_t enqueue_integrate(rk4_chain *h, int kernel, void *state, void *comp,
         // ntiles counts the full tiles (or, unpacked, every tile); the packed tiles follow them
         // in the same launch
         j.bt = dev_ktables(h, ws, L, ki);
-        j.tile_prefix = j.bt.full_prefix;
         j.ntiles = j.bt.nfull;
       } else {
         j.ntiles = tiles_for(h, j.G);
@@ -991,6 +1016,7 @@ int rk4_debug_barrier_timeout(rk4_chain *h, void *state, void *comp, void *ws, s
   if (prepare_tables(h, P.kval, W) != cudaSuccess) return RK4_ECUDA;
   char *w = static_cast<char *>(ws);
   if (upload_tables(h, w, L, h->stream) != cudaSuccess) return RK4_ECUDA;
+  if (fill_tile_tables(h, w, L, 1, h->stream) != cudaSuccess) return RK4_ECUDA;
   PersistentJob j{};
   j.bufA = state;
   j.bufB = w + L.state;

@@ -63,10 +63,14 @@ struct SegDesc {
 // and the packed tiles (pack_prefix: first segment of each packed tile, npacked + 1 entries,
 // into segs).  The kernels process the packed tiles first.  A chain of n sites has
 // floor(n / G) full tiles and, when G does not divide n, one segment.
+// tile_chain, when not null, holds for each full tile its chain and chain-local tile index
+// (filled on the device from full_prefix before the launches), so that a tile finds its chain
+// with one load instead of a search of full_prefix.
 struct BatchTiles {
   const int32_t *full_prefix;
   const int32_t *pack_prefix;
   const SegDesc *segs;
+  const int2 *tile_chain;
   int64_t nfull;
   int64_t npacked;
 };
@@ -77,12 +81,12 @@ struct BlockedJob {
   void *out;         // state written by this launch
   const void *cin;   // Kahan compensation read (FP32) or NULL
   void *cout;        // Kahan compensation written
-  int nchains;       // 1: use `one`; >1: use `chains` / `tile_prefix`
+  int nchains;       // 1: use `one`; >1: use `chains` / `bt`
   ChainDesc one;
   const ChainDesc *chains;      // device table (batches)
-  const int32_t *tile_prefix;   // device, nchains + 1 entries: first tile of each chain (unpacked batches)
-  BatchTiles bt;                // packed batches: full and packed tiles (used when `packed`)
-  int packed;                   // 1: the batch's tiles follow `bt`, 0: `tile_prefix`
+  BatchTiles bt;                // batches: the tiles of the launch (full_prefix counts every tile
+                                // of a chain when the batch is not packed)
+  int packed;                   // 1: packed tiles (bt.npacked of them) precede the full tiles
   int K;                        // steps in this launch
   int G;                        // interior sites per tile
   int64_t ntiles;               // tiles in the launch (a packed batch: its full tiles, beside bt.npacked)
@@ -167,6 +171,9 @@ cudaError_t launch_ghost_copy(void *state, void *comp, const GhostPair *pairs, i
 // Copy `bytes` between two 16-byte-aligned buffers with a kernel (either side may be mapped
 // page-locked host memory, given by its device pointer).
 cudaError_t launch_copy(void *dst, const void *src, size_t bytes, cudaStream_t st);
+// Fill tile_chain[t] = (chain, t - prefix[chain]) for the ntiles tiles numbered by prefix
+// (nchains + 1 entries, the first tile of each chain).
+cudaError_t launch_tile_chains(const int32_t *prefix, int nchains, int64_t ntiles, int2 *tile_chain, cudaStream_t st);
 cudaError_t launch_fill_uniform(void *dst, int64_t count, uint64_t seed, uint64_t start, bool fp32,
                                 cudaStream_t st);
 cudaError_t launch_gen_staged_step(int model, bool fp32, int range, const GenStagedJob &job, const CoefD &cf,

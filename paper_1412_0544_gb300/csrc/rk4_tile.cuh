@@ -705,6 +705,21 @@ __device__ __forceinline__ int find_chain_block(const int32_t *prefix, int nchai
   return *slot;
 }
 
+// Chain and chain-local tile index of full tile f of a batch launch: one load from the tile
+// table when the launch has one, else the block's search of the first-tile prefix.  Every
+// thread of the block calls it and gets the same answer.
+__device__ __forceinline__ int batch_chain(const BatchTiles &bt, int nchains, int64_t f, unsigned char *smem,
+                                           int64_t &local) {
+  if (bt.tile_chain) {
+    const int2 tc = __ldg(&bt.tile_chain[f]);
+    local = tc.y;
+    return tc.x;
+  }
+  const int ci = find_chain_block(bt.full_prefix, nchains, f, smem);
+  local = f - bt.full_prefix[ci];
+  return ci;
+}
+
 // Item `item` of a batch launch laid out by bt: the packed tiles first (they then run among the
 // full tiles instead of alone at the end), then the full tiles of the chains.
 template <typename R, int MODEL, int V, bool KAHAN, bool COH>
@@ -716,13 +731,12 @@ __device__ __forceinline__ void batch_item(const R *__restrict__ in, R *__restri
     packed_tile_item<R, MODEL, V, KAHAN, COH>(in, out, cin, cout, chains, bt.segs, bt.pack_prefix[item],
                                               bt.pack_prefix[item + 1], K, cf, smem, sites, hdr);
   } else {
-    const int64_t f = item - bt.npacked;
-    const int ci = find_chain_block(bt.full_prefix, nchains, f, smem);
+    int64_t local;
+    const int ci = batch_chain(bt, nchains, item - bt.npacked, smem, local);
     const ChainDesc ch = chains[ci];
     Coef<R> c = cf;
     c.kappa = (R)ch.kappa;
-    tile_item<R, MODEL, V, KAHAN, COH, false, true>(in, out, cin, cout, ch, f - bt.full_prefix[ci], K, G, c, smem,
-                                                    sites, hdr);
+    tile_item<R, MODEL, V, KAHAN, COH, false, true>(in, out, cin, cout, ch, local, K, G, c, smem, sites, hdr);
   }
 }
 

@@ -85,3 +85,31 @@ def test_packed_batch_many_tiny_chains(rk, gh):
             assert np.array_equal(got, st), (kernel, tiling)
     ref = oracle.batch_rk4_integrate(y0, lengths, kappa, bcs, nsteps=24)
     assert cf.rel_inf(st, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_without_tile_table_bitwise_equals_staged(rk, gh, precision):
+    """A tile finds its chain in a table of the launch's full tiles, which the workspace holds for
+    tiles of at least 64 interior sites.  At 64 x 2 x 8 (W = 128, halo 32 per side, G = 61 in
+    FP32 and 63 in FP64 after the 16-byte window alignment) these long chains have more full
+    tiles than the table holds, so the launches search the first-tile prefix instead; both ways
+    must give the staged kernel's result bit for bit."""
+    fp32 = precision == rk.RK4_FP32_KAHAN
+    lengths = np.array([100000, 70001, 5, 3000, 1], dtype=np.int64)
+    G = 61 if fp32 else 63
+    assert sum(n // G for n in lengths) > lengths.sum() // 64 + lengths.size  # beyond the table
+    kappa = np.array([1.0, 0.7, 1.3, 0.9, 1.1])
+    bcs = np.array([0, 1, 0, 1, 0], dtype=np.int8)
+    y0 = ci.uniform_state(int(lengths.sum()), 3, seed=620)
+    if fp32:
+        y0 = y0.astype(np.float32)
+    T = 21
+    st, cst = gh.gpu_run(y0, precision=precision, nsteps=T, lengths=lengths, kappas=kappa, bcs=bcs,
+                         kernel=rk.RK4_KERNEL_STAGED, return_comp=True)
+    for kernel in (rk.RK4_KERNEL_BLOCKED, rk.RK4_KERNEL_PERSISTENT):
+        for tiling in [(64, 2, 8), (256, 4, 2)]:  # without and with the table
+            got, cgot = gh.gpu_run(y0, precision=precision, nsteps=T, lengths=lengths, kappas=kappa, bcs=bcs,
+                                   kernel=kernel, tiling=tiling, return_comp=True)
+            assert np.array_equal(got, st), (kernel, tiling)
+            if fp32:
+                assert np.array_equal(cgot, cst), (kernel, tiling)
