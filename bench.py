@@ -81,7 +81,17 @@ FP32K_INST_PER_SITE_STEP = 58    # the update: 4 operations per component instea
 # tiling recorded with it; any other combination reports null.  A launch's traffic is
 # proportional to the sites it advances (one read and one write of each tile), so a capture at
 # N = 2^24 scales to the N = 2^27 workload by the site count.
-TRAFFIC = {}
+TRAFFIC = {
+    ("9b4eed5e250b63cb", "256,4,1"): (402923008 + 357651200, 1 << 24),
+    ("9b4eed5e250b63cb", "128,4,1"): (402787840 + 356530944, 1 << 24),
+    ("9b4eed5e250b63cb", "512,2,1"): (402862848 + 357082368, 1 << 24),
+    ("9b4eed5e250b63cb", "128,8,1"): (402874112 + 356882432, 1 << 24),
+    ("9b4eed5e250b63cb", "256,4,2"): (402821376 + 356387328, 1 << 24),
+    ("9b4eed5e250b63cb", "128,4,2"): (403012352 + 356921344, 1 << 24),
+    ("9b4eed5e250b63cb", "512,2,2"): (402769152 + 357067008, 1 << 24),
+    ("9b4eed5e250b63cb", "128,8,2"): (402909952 + 356694272, 1 << 24),
+    ("9b4eed5e250b63cb", "256,8,2"): (402850816 + 356891904, 1 << 24),
+}
 
 
 def traffic_per_launch(khash: str, tiling: dict, n: int):
