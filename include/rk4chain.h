@@ -38,7 +38,8 @@
  *     between calls (it is part of the integrator's state).  NULL for RK4_FP64.
  *   - ws / ws_bytes: a device workspace of at least rk4_chain_workspace_bytes() bytes,
  *     256-byte aligned; contents need not be preserved between calls.  It holds the
- *     ping-pong copy of the state, reduction partials and the device status word.
+ *     ping-pong copy of the state, reduction partials, the device status word and, for a
+ *     batch, its chain and tile tables (8 bytes per tile of at least 64 interior sites).
  *   - Device-side errors (a NaN or infinity in a state that an integration stores or a
  *     reduction reads, a barrier wait that ran out of time, in a debug build an index out of
  *     range) are latched in the status word inside ws and reported by rk4_chain_status().
