@@ -126,6 +126,42 @@ def test_generic_fp32_kahan(rk):
     assert err <= FP32_KAHAN_TOL
 
 
+@pytest.mark.parametrize("shape", ["dopri5", "rk4"])
+@pytest.mark.parametrize("model,bc,kappa2", [(ROE, FIX, 0.7), (ROE, PER, 0.0), (HAR, FIX, 0.0), (HAR, PER, 0.6)])
+def test_generic_fp32_compiled_shapes_bitwise(rk, shape, model, bc, kappa2):
+    """The tableau shapes with compiled FP32 tile kernels (4 sites per thread) issue their
+    arithmetic on packed pairs of sites; every model, boundary (fixed ends mask ghost sites) and
+    coupling range must still give the scalar one-stage-per-launch kernel's bits, state and
+    compensation alike."""
+    A, b, _ = P.TABLEAUX[shape]
+    D = 3 if model == ROE else 2
+    y0 = ci.uniform_state(5003, D, seed=370 + model + 2 * bc).astype(np.float32)
+    nsteps = 41
+    st, cst = run(rk, y0, model=model, bc=bc, prec=1, nsteps=nsteps, A=A, b=b, kappa2=kappa2,
+                  kernel=rk.RK4_KERNEL_STAGED, with_comp=True)
+    for tiling in [(128, 4, 2), (64, 4, 3), (512, 4, 1)]:
+        got, cgot = run(rk, y0, model=model, bc=bc, prec=1, nsteps=nsteps, A=A, b=b, kappa2=kappa2,
+                        kernel=rk.RK4_KERNEL_BLOCKED, tiling=tiling, with_comp=True)
+        assert np.array_equal(got, st) and np.array_equal(cgot, cst), tiling
+    ref = oracle.rk_integrate(y0.astype(np.float64), A, b, model, bc, 0.01, nsteps,
+                              oracle.params(kappa=1.0, omega0=0.8, kappa2=kappa2))
+    assert cf.rel_inf(st - cst, ref) <= FP32_KAHAN_TOL
+
+
+def test_generic_fp32_batch_bitwise(rk):
+    """Uneven FP32 chains with the Dormand-Prince 5 shape and second neighbours (packed pairs,
+    per-chain coupling, mixed ends) against the staged kernel, bit for bit."""
+    A, b, _ = P.TABLEAUX["dopri5"]
+    lengths, kappa, bcs = ci.batch_spec(30, seed=380, nmin=1, nmax=3000)
+    y0 = ci.uniform_state(int(lengths.sum()), 3, seed=381).astype(np.float32)
+    st, cst = run(rk, y0, prec=1, nsteps=33, A=A, b=b, kappa2=0.4, lengths=lengths, kappas=kappa, bcs=bcs,
+                  kernel=rk.RK4_KERNEL_STAGED, with_comp=True)
+    for tiling in [(128, 4, 2), (256, 4, 4)]:
+        got, cgot = run(rk, y0, prec=1, nsteps=33, A=A, b=b, kappa2=0.4, lengths=lengths, kappas=kappa, bcs=bcs,
+                        kernel=rk.RK4_KERNEL_BLOCKED, tiling=tiling, with_comp=True)
+        assert np.array_equal(got, st) and np.array_equal(cgot, cst), tiling
+
+
 def test_generic_batch(rk):
     A, b, _ = P.TABLEAUX["kutta3"]
     lengths, kappa, bcs = ci.batch_spec(40, seed=360, nmin=1, nmax=2000)
