@@ -94,6 +94,25 @@ def test_persistent_batch_with_tails(rk, prec):
         assert same(got, ref)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_persistent_batch_many_tiles_per_block(rk, prec):
+    """A batch large enough that every resident block draws several full tiles per time block
+    (and the block order in which tiles are drawn differs from run to run): bit for bit the
+    staged result, over repeated runs, with periodic and fixed chains, wrapped end windows,
+    packed pieces and a tail time block of another k."""
+    lengths, kappa, bcs = ci.batch_spec(72, seed=994, nmin=2000, nmax=90000)
+    y0 = ci.uniform_state(int(lengths.sum()), 3, seed=995)
+    if prec:
+        y0 = y0.astype(np.float32)
+    b = (lengths, kappa, bcs)
+    nsteps = 4 * 4 + 2  # four time blocks of k = 4, then a tail of k = 2
+    ref = run(rk, y0, prec=prec, nsteps=nsteps, kernel=rk.RK4_KERNEL_STAGED, batch=b)
+    for tiling in [(128, 4, 4), (256, 4, 4), (64, 2, 4), (256, 8, 4)]:
+        for _ in range(2):
+            got = run(rk, y0, prec=prec, nsteps=nsteps, kernel=rk.RK4_KERNEL_PERSISTENT, tiling=tiling, batch=b)
+            assert same(got, ref), tiling
+
+
 def test_persistent_harmonic_many_small_tiles(rk):
     """128 x 1 tiles with k = 4 (G = 96): thousands of items per time block, 100 time blocks."""
     n = 200003
