@@ -26,6 +26,8 @@ def main():
     ap.add_argument("--tableau", choices=["rk4", "dopri5"], default="rk4",
                     help="dopri5: the generic kernels with Dormand and Prince's 7-stage tableau")
     ap.add_argument("--kappa2", type=float, default=0.0, help="second-neighbour coupling (generic kernels)")
+    ap.add_argument("--het", action="store_true",
+                    help="heterogeneous chain: per-site a, b, c, kappa drawn as in bench.py (Eq. (1))")
     args = ap.parse_args()
 
     import torch
@@ -56,6 +58,14 @@ def main():
         rk.rk4_chain_set_tableau(h, bench.DOPRI5_A, bench.DOPRI5_B)
     if args.kappa2:
         rk.rk4_chain_set_coupling2(h, args.kappa2)
+    if args.het:
+        import numpy as np
+        import bench
+        u = ci.uniform01(bench.SEED, 9, 0, 4 * total).reshape(total, 4)
+        sp = torch.from_numpy(np.stack([0.15 + 0.1 * u[:, 0], 0.8 + 0.4 * u[:, 1], 8.0 + 2.0 * u[:, 2],
+                                        0.5 + 1.5 * u[:, 3]], axis=1))
+        sp = sp.to(torch.float64 if prec == rk.RK4_FP64 else torch.float32).cuda()
+        rk.rk4_chain_set_site_params(h, sp)
     rk.rk4_chain_set_tiling(h, *[int(x) for x in args.tiling.split(",")])
     rk.rk4_chain_set_option(h, rk.RK4_OPT_GRAPHS, 0)
     dtype = torch.float64 if prec == rk.RK4_FP64 else torch.float32

@@ -114,6 +114,23 @@ def test_het_fp32_kahan(rk):
     assert err <= FP32_KAHAN_TOL
 
 
+@pytest.mark.parametrize("model,bc", [(ROE, FIX), (HAR, PER), (HAR, FIX)])
+def test_het_fp32_kahan_models_and_ends_bitwise(rk, model, bc):
+    """FP32-Kahan heterogeneous tiles on packed pairs of sites, whose per-site coefficients
+    are read per stage from shared memory in pair order: both models (four and two per-site
+    coefficients), fixed ends (ghost sites), against the staged kernel bit for bit."""
+    D = 3 if model == ROE else 2
+    n = 20011
+    y0 = ci.uniform_state(n, D, seed=435 + model + 2 * bc).astype(np.float32)
+    sp = P.het_params(n, model, 436 + bc).astype(np.float32)
+    st, cst = run(rk, y0, sp, model=model, bc=bc, prec=1, nsteps=64, kernel=rk.RK4_KERNEL_STAGED, with_comp=True)
+    for tiling in [(256, 4, 4), (128, 2, 8), (64, 4, 2)]:
+        got, cgot = run(rk, y0, sp, model=model, bc=bc, prec=1, nsteps=64, tiling=tiling, with_comp=True)
+        assert np.array_equal(got, st) and np.array_equal(cgot, cst), tiling
+    ref = oracle.rk4_integrate_het(y0.astype(np.float64), sp.astype(np.float64), model, bc, 0.01, 64)
+    assert cf.rel_inf(st - cst, ref) <= FP32_KAHAN_TOL
+
+
 def test_het_batch(rk):
     lengths, kappa, bcs = ci.batch_spec(50, seed=440, nmin=1, nmax=3000)
     total = int(lengths.sum())
