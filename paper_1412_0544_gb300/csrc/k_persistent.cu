@@ -47,7 +47,20 @@ __device__ __forceinline__ bool grid_barrier(WsHeader *hdr, long long timeout_ns
   return ok != 0;
 }
 
+// A packed tile of a batch (the segments of item p).  Not inlined, as in the one-shot blocked
+// kernel: the segment bookkeeping then takes registers only inside this call, and the full-tile
+// path, which runs nearly every item, keeps its own allocation (inlined, the FP32 batch kernel
+// spilled at the 64-register cap of four resident blocks per SM).
 template <typename R, int MODEL, int V, bool KAHAN>
+__device__ __noinline__ void persistent_packed_call(const R *in, R *out, const R *cin, R *cout,
+                                                    const ChainDesc *chains, const SegDesc *segs,
+                                                    const int32_t *pack_prefix, int64_t p, int K, Coef<R> cf,
+                                                    unsigned char *smem, int64_t sites, WsHeader *hdr) {
+  packed_tile_item<R, MODEL, V, KAHAN, true>(in, out, cin, cout, chains, segs, pack_prefix[p], pack_prefix[p + 1], K,
+                                             cf, smem, sites, hdr);
+}
+
+template <typename R, int MODEL, int V, bool KAHAN, bool BATCH>
 __global__ void __launch_bounds__(max_threads_for(V), (V >= 2 && KAHAN) ? 2 : 1)  // FP32: two resident blocks
     k_persistent(PersistentJob job, Coef<R> cf) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -70,8 +83,11 @@ __global__ void __launch_bounds__(max_threads_for(V), (V >= 2 && KAHAN) ? 2 : 1)
     if (threadIdx.x == 0) s_item = (long long)atomicAdd(ctr, 1ull);
     __syncthreads();
     for (int64_t item = s_item; item < ntiles;) {
-      if (job.nchains == 1)
+      if constexpr (!BATCH)
         tile_item<R, MODEL, V, KAHAN, true>(in, out, cin, cout, job.one, item, K, G, cf, smem, job.total, job.hdr);
+      else if (item < job.bt[ki].npacked)
+        persistent_packed_call<R, MODEL, V, KAHAN>(in, out, cin, cout, job.chains, job.bt[ki].segs,
+                                                   job.bt[ki].pack_prefix, item, K, cf, smem, job.total, job.hdr);
       else
         batch_item<R, MODEL, V, KAHAN, true>(in, out, cin, cout, job.chains, job.nchains, job.bt[ki], item, K, G, cf,
                                              smem, job.total, job.hdr);
@@ -88,8 +104,10 @@ __global__ void __launch_bounds__(max_threads_for(V), (V >= 2 && KAHAN) ? 2 : 1)
 
 template <typename R, int MODEL, int V, bool KAHAN>
 static cudaError_t setup_attr() {
-  static PerDevice attr;
-  return set_smem_limit_once(k_persistent<R, MODEL, V, KAHAN>, 200 * 1024, attr);
+  static PerDevice attr, attr_b;
+  const cudaError_t e = set_smem_limit_once(k_persistent<R, MODEL, V, KAHAN, false>, 200 * 1024, attr);
+  if (e != cudaSuccess) return e;
+  return set_smem_limit_once(k_persistent<R, MODEL, V, KAHAN, true>, 200 * 1024, attr_b);
 }
 
 template <typename R, int MODEL, int V, bool KAHAN>
@@ -108,7 +126,8 @@ static cudaError_t launch_one(int block, int grid, const PersistentJob &job, con
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_persistent<R, MODEL, V, KAHAN>, job, cf);
+  if (job.nchains > 1) return cudaLaunchKernelEx(&cfg, k_persistent<R, MODEL, V, KAHAN, true>, job, cf);
+  return cudaLaunchKernelEx(&cfg, k_persistent<R, MODEL, V, KAHAN, false>, job, cf);
 }
 
 template <typename R, int MODEL, int V, bool KAHAN>
@@ -116,10 +135,13 @@ static int max_grid_one(int block) {
   if (setup_attr<R, MODEL, V, KAHAN>() != cudaSuccess) return 0;
   int per_sm = 0;
   const size_t smem = blocked_smem_bytes(MODEL, KAHAN, V, block);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<R, MODEL, V, KAHAN>, block, smem) !=
-      cudaSuccess)
+  int per_sm_b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<R, MODEL, V, KAHAN, false>, block, smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, k_persistent<R, MODEL, V, KAHAN, true>, block, smem) !=
+          cudaSuccess)
     return 0;
-  return per_sm * sm_count();
+  return std::min(per_sm, per_sm_b) * sm_count();  // a grid that stays co-resident with either form
 }
 
 #define RK4_DISPATCH_V(FN, ...)                                                                   \
