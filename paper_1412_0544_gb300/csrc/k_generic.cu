@@ -162,10 +162,9 @@ __device__ __forceinline__ void gen_tile_advance(R (&y)[V][Dim<MODEL>::D], R (&c
       tv.y = ext[V + 1];
       head[tid] = hv;
       tail[tid] = tv;
-      // each thread reads only its neighbour threads' slots: in FP64, bound by the FP64 pipe,
-      // the streaming form waits for the neighbouring warps only (measured +4.6 % for
-      // Dormand-Prince 5; in FP32, bound by instruction issue, the two barriers per stage cost
-      // 22 %)
+      // each thread reads only its neighbour threads' slots: in FP64 the streaming form waits
+      // for the neighbouring warps only (measured +4.6 % for Dormand-Prince 5); in FP32 the two
+      // named barriers per stage cost 22 %, so it keeps the block-wide one
       if constexpr (SHAPE != 0 && sizeof(R) == 8) neighbour_warp_sync(); else __syncthreads();
       {
         const R2 l = tail[lt];

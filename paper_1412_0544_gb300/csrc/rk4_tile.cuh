@@ -125,8 +125,10 @@ __device__ __forceinline__ void neighbour_warp_sync() {
 }
 
 // The barrier of a tile kernel's neighbour exchange, where each thread (warp) reads only the
-// slots of its neighbours: FP64 waits for the neighbouring warps only (neighbour_warp_sync);
-// FP32, bound by instruction issue, keeps the one block-wide barrier per stage.
+// slots of its neighbours: FP64 waits for the neighbouring warps only (neighbour_warp_sync,
+// measured 7 % faster: the warps of a block no longer enter each stage's FP64 stream in lock
+// step); FP32 keeps the one block-wide barrier per stage (the two named barriers measured 16-28 %
+// slower there).
 template <typename R> __device__ __forceinline__ void stage_sync() {
   if constexpr (sizeof(R) == 8) neighbour_warp_sync(); else __syncthreads();
 }
