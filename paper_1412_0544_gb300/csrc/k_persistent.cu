@@ -60,6 +60,21 @@ __device__ __noinline__ void persistent_packed_call(const R *in, R *out, const R
                                              cf, smem, sites, hdr);
 }
 
+// One full tile, of a single chain or (BATCH) of a batch, as a call of its own: the tile's
+// arithmetic then gets the register budget it has in the one-shot blocked kernel, instead of
+// sharing it with the persistent loop's state (time block, item, buffers), which the call saves
+// once per tile.
+template <typename R, int MODEL, int V, bool KAHAN, bool BATCH>
+__device__ __noinline__ void persistent_tile_call(const PersistentJob &job, int ki, const R *in, R *out,
+                                                  const R *cin, R *cout, int64_t item, int K, int G, Coef<R> cf,
+                                                  unsigned char *smem) {
+  if constexpr (!BATCH)
+    tile_item<R, MODEL, V, KAHAN, true>(in, out, cin, cout, job.one, item, K, G, cf, smem, job.total, job.hdr);
+  else
+    batch_item<R, MODEL, V, KAHAN, true>(in, out, cin, cout, job.chains, job.nchains, job.bt[ki], item, K, G, cf,
+                                         smem, job.total, job.hdr);
+}
+
 template <typename R, int MODEL, int V, bool KAHAN, bool BATCH>
 __global__ void __launch_bounds__(max_threads_for(V), (V >= 2 && KAHAN) ? 2 : 1)  // FP32: two resident blocks
     k_persistent(PersistentJob job, Coef<R> cf) {
@@ -83,14 +98,11 @@ __global__ void __launch_bounds__(max_threads_for(V), (V >= 2 && KAHAN) ? 2 : 1)
     if (threadIdx.x == 0) s_item = (long long)atomicAdd(ctr, 1ull);
     __syncthreads();
     for (int64_t item = s_item; item < ntiles;) {
-      if constexpr (!BATCH)
-        tile_item<R, MODEL, V, KAHAN, true>(in, out, cin, cout, job.one, item, K, G, cf, smem, job.total, job.hdr);
-      else if (item < job.bt[ki].npacked)
+      if (BATCH && item < job.bt[ki].npacked)
         persistent_packed_call<R, MODEL, V, KAHAN>(in, out, cin, cout, job.chains, job.bt[ki].segs,
                                                    job.bt[ki].pack_prefix, item, K, cf, smem, job.total, job.hdr);
       else
-        batch_item<R, MODEL, V, KAHAN, true>(in, out, cin, cout, job.chains, job.nchains, job.bt[ki], item, K, G, cf,
-                                             smem, job.total, job.hdr);
+        persistent_tile_call<R, MODEL, V, KAHAN, BATCH>(job, ki, in, out, cin, cout, item, K, G, cf, smem);
       // both end with a barrier, so every thread has read s_item before it is rewritten
       if (threadIdx.x == 0) s_item = (long long)atomicAdd(ctr, 1ull);
       __syncthreads();
