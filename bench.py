@@ -48,11 +48,10 @@ HBM_GBS_FALLBACK = 6800.0
 # Arithmetic peaks for the ALU rooflines, measured by pipe_probe.cu beside this file (run
 # by bench.py itself on rank 0 before the workload, so the denominator comes from the same GPU
 # and clocks; the constants below, from an earlier probe run on a GB300 at 2070 MHz, are the
-# fallback when the probe cannot run).  The classical RK4 Roessler step issues 41 DFMA and
-# 8 DADD per site-step in FP64 (4 x (5 FMA + 2 ADD) slope, 9 FMA stage states, 12 FMA
-# update).  Every addition can be issued as an exact FMA (a*1+b), so 49 instructions at the
-# DFMA rate bound the step, and the roof is the DFMA rate.  FP32: the larger of the scalar and
-# packed (f32x2) FMA lane rates.
+# fallback when the probe cannot run).  The classical RK4 Roessler step issues 49 DFMA per
+# site-step in FP64 (4 x 7 slope, whose two additions are issued as exact FMAs a*1+b, 9 stage
+# states, 12 update), so the roof is the DFMA rate.  FP32: the larger of the scalar and packed
+# (f32x2) FMA lane rates.
 FP64_INST_PEAK = 0.6272e12
 FP32_INST_PEAK = 40.12e12
 PEAK_SOURCE = "fallback constants from an earlier pipe_probe run"
@@ -74,7 +73,7 @@ def probe_peaks():
         return {"error": str(e)[:200]}
 
 
-FP64_INST_PER_SITE_STEP = 49     # 41 DFMA + 8 DADD
+FP64_INST_PER_SITE_STEP = 49     # DFMA (the slope's 8 additions issued as a * 1 + b)
 FP32K_INST_PER_SITE_STEP = 58    # the update: 4 operations per component instead of 1 FMA
 # DRAM traffic (read + write bytes) per launch of the FP64 blocked kernel from one ncu capture,
 # with the chain length it was taken at: valid only for the kernel code (kernel_hash) and the
@@ -82,15 +81,15 @@ FP32K_INST_PER_SITE_STEP = 58    # the update: 4 operations per component instea
 # proportional to the sites it advances (one read and one write of each tile), so a capture at
 # N = 2^24 scales to the N = 2^27 workload by the site count.
 TRAFFIC = {
-    ("9b4eed5e250b63cb", "256,4,1"): (402923008 + 357651200, 1 << 24),
-    ("9b4eed5e250b63cb", "128,4,1"): (402787840 + 356530944, 1 << 24),
-    ("9b4eed5e250b63cb", "512,2,1"): (402862848 + 357082368, 1 << 24),
-    ("9b4eed5e250b63cb", "128,8,1"): (402874112 + 356882432, 1 << 24),
-    ("9b4eed5e250b63cb", "256,4,2"): (402821376 + 356387328, 1 << 24),
-    ("9b4eed5e250b63cb", "128,4,2"): (403012352 + 356921344, 1 << 24),
-    ("9b4eed5e250b63cb", "512,2,2"): (402769152 + 357067008, 1 << 24),
-    ("9b4eed5e250b63cb", "128,8,2"): (402909952 + 356694272, 1 << 24),
-    ("9b4eed5e250b63cb", "256,8,2"): (402850816 + 356891904, 1 << 24),
+    ("24e57e0265074389", "256,4,1"): (402771968 + 357428224, 1 << 24),
+    ("24e57e0265074389", "128,4,1"): (402821632 + 356577792, 1 << 24),
+    ("24e57e0265074389", "512,2,1"): (402830848 + 356819456, 1 << 24),
+    ("24e57e0265074389", "128,8,1"): (403226624 + 356647424, 1 << 24),
+    ("24e57e0265074389", "256,4,2"): (402761472 + 357003008, 1 << 24),
+    ("24e57e0265074389", "128,4,2"): (402859776 + 356683008, 1 << 24),
+    ("24e57e0265074389", "512,2,2"): (402838272 + 357778944, 1 << 24),
+    ("24e57e0265074389", "128,8,2"): (402945792 + 357322496, 1 << 24),
+    ("24e57e0265074389", "256,8,2"): (402975232 + 357140224, 1 << 24),
 }
 
 

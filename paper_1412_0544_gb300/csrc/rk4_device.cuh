@@ -49,18 +49,22 @@ __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b);
 __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
 // Coefficients of one chain in the working precision R.  h2 = dt/2, h1 = dt, dt6 = dt/6,
-// dt3 = dt/3 are rounded once on the host, so every kernel sees identical constants.
+// dt3 = dt/3 are rounded once on the host, so every kernel sees identical constants.  one = 1,
+// passed at run time: the FP64 slope issues its additions as a x one + b, the exact sum
+// rounded once like a DADD, on the DFMA rate (a DADD issues at 0.84 of it; with a literal 1
+// the compiler would turn the FMA back into an addition).
 template <typename R> struct Coef {
-  R a, b, c, kappa, w2, h2, h1, dt6, dt3;
+  R a, b, c, kappa, w2, h2, h1, dt6, dt3, one;
 };
 
 // Slope (Eq. (3)) of one site from its stage state u and its neighbours' coupling
 // coordinates xl, xr (already resolved by the boundary condition).
 template <typename R, int MODEL>
 __device__ __forceinline__ void slope(const R *u, R xl, R xr, const Coef<R> &cf, R *k) {
-  const R lap = fma(R(-2), u[0], add(xl, xr));
+  constexpr bool kFmaAdd = sizeof(R) == 8;  // FP64: additions as DFMA (see Coef::one)
+  const R lap = fma(R(-2), u[0], kFmaAdd ? fma(xl, cf.one, xr) : add(xl, xr));
   if constexpr (MODEL == ROESSLER) {
-    k[0] = fma(cf.kappa, lap, -add(u[1], u[2]));
+    k[0] = fma(cf.kappa, lap, -(kFmaAdd ? fma(u[1], cf.one, u[2]) : add(u[1], u[2])));
     k[1] = fma(cf.a, u[1], u[0]);
     if constexpr (sizeof(R) == 8)
       k[2] = fma(u[2], u[0], fma(-cf.c, u[2], cf.b));  // two DFMA, no DADD

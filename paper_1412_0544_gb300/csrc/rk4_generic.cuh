@@ -81,10 +81,11 @@ __device__ __forceinline__ void slope_gen(const R *u, R xl, R xr, R xl2, R xr2, 
   if constexpr (RANGE == 1) {
     slope<R, MODEL>(u, xl, xr, cf, k);
   } else {
-    const R lap = fma(R(-2), u[0], add(xl, xr));
-    const R lap2 = fma(R(-2), u[0], add(xl2, xr2));
+    constexpr bool kFmaAdd = sizeof(R) == 8;  // FP64: additions as DFMA (see Coef::one)
+    const R lap = fma(R(-2), u[0], kFmaAdd ? fma(xl, cf.one, xr) : add(xl, xr));
+    const R lap2 = fma(R(-2), u[0], kFmaAdd ? fma(xl2, cf.one, xr2) : add(xl2, xr2));
     if constexpr (MODEL == ROESSLER) {
-      k[0] = fma(cf.kappa, lap, fma(kappa2, lap2, -add(u[1], u[2])));
+      k[0] = fma(cf.kappa, lap, fma(kappa2, lap2, -(kFmaAdd ? fma(u[1], cf.one, u[2]) : add(u[1], u[2]))));
       k[1] = fma(cf.a, u[1], u[0]);
       if constexpr (sizeof(R) == 8)
         k[2] = fma(u[2], u[0], fma(-cf.c, u[2], cf.b));  // as slope(): two DFMA, no DADD

@@ -745,7 +745,7 @@ __device__ __forceinline__ void batch_item(const R *__restrict__ in, R *__restri
 template <typename R> __host__ __device__ inline Coef<R> to_coef(const CoefD &c, double kappa) {
   Coef<R> r;
   r.a = (R)c.a; r.b = (R)c.b; r.c = (R)c.c; r.kappa = (R)kappa; r.w2 = (R)c.w2;
-  r.h2 = (R)c.h2; r.h1 = (R)c.h1; r.dt6 = (R)c.dt6; r.dt3 = (R)c.dt3;
+  r.h2 = (R)c.h2; r.h1 = (R)c.h1; r.dt6 = (R)c.dt6; r.dt3 = (R)c.dt3; r.one = R(1);
   return r;
 }
 
